@@ -1,0 +1,305 @@
+"""Seeded synthetic workloads shaped like the paper's benchmark problems.
+
+This module only builds inputs: grid descriptions, species parameters and
+initial states (distribution functions sampled at velocity cell centres,
+analytic fluid moments, Yee fields from a vector potential). It holds none of
+the solver's arithmetic and is the one module that both the CUDA path and the
+CPU oracle's tests draw their inputs from.
+
+Workloads (all synthetic; the paper's runs use no external dataset):
+
+* ``landau``  -- 1D1V electrostatic Landau damping (paper Sec. 3.1):
+  f0 = exp(-v^2/2)/sqrt(2 pi) (1 + alpha cos(k x)), electrons on a fixed ion
+  background, electrostatic normalisation (omega_p, lambda_D, v_t).
+* ``harris``  -- 2D3V GEM/Harris-sheet reconnection (paper Sec. 3.3):
+  n = sech^2(y/lambda) + n_b, B_x = tanh(y/lambda) + dB_x, B_y = dB_y,
+  n (T_e + T_i) = B0^2/2, T_i/T_e = 5, current split with
+  |u_z,i / u_z,e| = T_i/T_e and opposite signs, periodic x, walls in y.
+* ``asym_sheet`` -- asymmetric magnetopause-like sheet (structure of the
+  magnetotail setup of Sec. 4.1 with a density step).
+* ``random_blocks`` -- positive random phase-space data for kernel tests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class SpeciesCfg:
+    name: str
+    q: float
+    m: float
+    nv: tuple          # (nvx, nvy, nvz); 1D1V: (nv, 1, 1)
+    vmin: tuple
+    vmax: tuple
+
+    @property
+    def dv(self):
+        return tuple((self.vmax[a] - self.vmin[a]) / self.nv[a] for a in range(3))
+
+    def vcentres(self, axis):
+        return self.vmin[axis] + (np.arange(self.nv[axis]) + 0.5) * self.dv[axis]
+
+    @property
+    def vblock(self):
+        return self.nv[0] * self.nv[1] * self.nv[2]
+
+
+@dataclasses.dataclass
+class Config:
+    name: str
+    nvdim: int
+    nx: int
+    ny: int
+    x0: float
+    lx: float
+    y0: float
+    ly: float
+    bc_y: int                  # 0 periodic, 1 conducting/reflecting walls
+    species: List[SpeciesCfg]
+    dt: float
+    steps: int
+    c: Optional[float] = None  # speed of light (None: electrostatic)
+    ion_background: float = 0.0  # fixed neutralising density (1D1V)
+    precision: int = 32
+    nshear: int = 5
+    fit_tol: float = 1e-11
+    fit_max_iter: int = 20
+    splitting: str = "lie"     # "lie": x, y, v ; "strang": x/2, y/2, v, y/2, x/2
+
+    @property
+    def dx(self):
+        return self.lx / self.nx
+
+    @property
+    def dy(self):
+        return self.ly / self.ny
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny
+
+    def phase_cells(self):
+        return sum(self.ncell * s.vblock for s in self.species)
+
+
+# ----------------------------------------------------------------- Landau ---
+
+def landau(nx=64, nv=32, vmax=6.0, alpha=0.01, k=0.5, dt=0.05, steps=200,
+           precision=64) -> Config:
+    """1D1V linear Landau damping (Sec. 3.1) on one wavelength [0, 2 pi / k)."""
+    lx = 2.0 * math.pi / k  # one wavelength: 4 pi for k = 0.5
+    sp = SpeciesCfg("e", -1.0, 1.0, (nv, 1, 1), (-vmax, 0.0, 0.0), (vmax, 1.0, 1.0))
+    cfg = Config("landau_1d1v_%dx%d" % (nx, nv), 1, nx, 1, 0.0, lx, 0.0, 1.0, 0, [sp], dt, steps,
+                 c=None, ion_background=1.0, precision=precision, splitting="strang")
+    cfg.alpha = alpha
+    cfg.k = k
+    return cfg
+
+
+def landau_state(cfg: Config):
+    """f0 [nx][nv] sampled at cell centres, float64."""
+    sp = cfg.species[0]
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    v = sp.vcentres(0)
+    f = (np.exp(-0.5 * v[None, :] ** 2) / math.sqrt(2 * math.pi)) * (1.0 + cfg.alpha * np.cos(cfg.k * x))[:, None]
+    return [np.ascontiguousarray(f)]
+
+
+# ----------------------------------------------------------------- Harris ---
+
+def harris(nx=128, ny=64, nv=20, lx=25.6, ly=12.8, mass_ratio=25.0, lam=0.5, nb=0.2,
+           psi0=0.1, ti_te=5.0, c=20.0, vbox_vth=5.0, steps=500, precision=32,
+           dt=None) -> Config:
+    """2D3V GEM/Harris sheet (Sec. 3.3) on [-lx/2, lx/2] x [-ly/2, ly/2]."""
+    te = 0.5 / (1.0 + ti_te)
+    ti = 0.5 - te
+    species = []
+    for name, q, m, t in (("e", -1.0, 1.0 / mass_ratio, te), ("i", 1.0, 1.0, ti)):
+        vth = math.sqrt(t / m)
+        vm = vbox_vth * vth
+        species.append(SpeciesCfg(name, q, m, (nv, nv, nv), (-vm, -vm, -vm), (vm, vm, vm)))
+        species[-1].T = t
+    dx, dy = lx / nx, ly / ny
+    if dt is None:
+        dt = 0.5 * min(dx, dy) / c
+    cfg = Config("harris_2d3v_%dx%d_v%d" % (nx, ny, nv), 3, nx, ny, -lx / 2, lx, -ly / 2, ly, 1,
+                 species, dt, steps, c=c, precision=precision)
+    cfg.lam, cfg.nb, cfg.psi0, cfg.kind = lam, nb, psi0, "harris"
+    return cfg
+
+
+def _harris_Az(cfg, x, y):
+    lam, psi0 = cfg.lam, cfg.psi0
+    return lam * np.log(np.cosh(y / lam)) + psi0 * np.cos(2 * math.pi * x / cfg.lx) * np.cos(math.pi * y / cfg.ly)
+
+
+def _harris_profiles(cfg, x, y):
+    """density n(x,y) and total current j_z(x,y) of the initial sheet"""
+    lam = cfg.lam
+    n = 1.0 / np.cosh(y / lam) ** 2 + cfg.nb
+    jz = -(1.0 / lam) / np.cosh(y / lam) ** 2 + cfg.psi0 * np.cos(2 * math.pi * x / cfg.lx) * np.cos(
+        math.pi * y / cfg.ly) * ((2 * math.pi / cfg.lx) ** 2 + (math.pi / cfg.ly) ** 2)
+    return n, jz
+
+
+def _cell_centres(cfg):
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    y = cfg.y0 + (np.arange(cfg.ny) + 0.5) * cfg.dy
+    X, Y = np.meshgrid(x, y)  # [ny][nx]
+    return X, Y
+
+
+def harris_drifts(cfg):
+    """u_z per species at cell centres: |u_z,i/u_z,e| = T_i/T_e, opposite signs."""
+    X, Y = _cell_centres(cfg)
+    n, jz = _harris_profiles(cfg, X, Y)
+    te, ti = cfg.species[0].T, cfg.species[1].T
+    ui = (ti / (ti + te)) * jz / n
+    ue = -(te / (ti + te)) * jz / n
+    return n, {"e": ue, "i": ui}
+
+
+def harris_state(cfg: Config, dtype=np.float64, species=None):
+    """Initial f per species, [ny][nx][nvz][nvy][nvx] sampled at velocity cell
+    centres (drifting isotropic Maxwellians)."""
+    n, drift = harris_drifts(cfg)
+    out = []
+    for sp in cfg.species:
+        if species is not None and sp.name not in species:
+            out.append(None)
+            continue
+        th = sp.T / sp.m
+        vx, vy, vz = sp.vcentres(0), sp.vcentres(1), sp.vcentres(2)
+        gxy = np.exp(-(vy[:, None] ** 2 + vx[None, :] ** 2) / (2 * th)).astype(dtype)
+        uz = drift[sp.name]
+        norm = (n / (2 * math.pi * th) ** 1.5).astype(dtype)
+        hz = np.exp(-((vz[None, None, :] - uz[:, :, None]) ** 2) / (2 * th)).astype(dtype)
+        f = np.empty((cfg.ny, cfg.nx, sp.nv[2], sp.nv[1], sp.nv[0]), dtype=dtype)
+        for j in range(cfg.ny):
+            np.multiply((norm[j][:, None] * hz[j])[:, :, None, None], gxy[None, None, :, :], out=f[j])
+        out.append(f)
+    return out
+
+
+def harris_fluid(cfg: Config):
+    """Analytic moments (n, nu, int v v f) of the initial drifting Maxwellians."""
+    n, drift = harris_drifts(cfg)
+    out = []
+    for sp in cfg.species:
+        th = sp.T / sp.m
+        U = np.zeros((cfg.ny, cfg.nx, 10))
+        uz = drift[sp.name]
+        U[..., 0] = n
+        U[..., 3] = n * uz
+        U[..., 4] = n * th
+        U[..., 7] = n * th
+        U[..., 9] = n * (th + uz * uz)
+        out.append(U.reshape(cfg.ncell, 10))
+    return out
+
+
+def yee_from_Az(cfg: Config, Az_fn, bz=0.0):
+    """Yee fields [6][ny+1][nx] (Ex, Ey, Ez, Bx, By, Bz) with B = curl(A_z z)
+    from the vector potential at the cell corners (discretely divergence
+    free); E = 0."""
+    nx, ny = cfg.nx, cfg.ny
+    xc = cfg.x0 + np.arange(nx + 1) * cfg.dx
+    yc = cfg.y0 + np.arange(ny + 1) * cfg.dy
+    XC, YC = np.meshgrid(xc, yc)  # [ny+1][nx+1]
+    A = Az_fn(cfg, XC, YC)
+    yee = np.zeros((6, ny + 1, nx))
+    # Bx(i, j+1/2) = dA/dy
+    yee[3, :ny, :] = (A[1:, :nx] - A[:-1, :nx]) / cfg.dy
+    # By(i+1/2, j) = -dA/dx
+    yee[4, :, :] = -(A[:, 1:] - A[:, :-1]) / cfg.dx
+    yee[5, :ny, :] = bz
+    return yee
+
+
+def harris_yee(cfg: Config):
+    return yee_from_Az(cfg, _harris_Az)
+
+
+# --------------------------------------------------------- asymmetric sheet ---
+
+def asym_sheet(nx=1024, ny=512, nv=12, lx=51.2, ly=25.6, mass_ratio=100.0, lam=0.5,
+               n_ratio=10.0, t_ratio=3.0, bguide=0.1, xi=0.01, c=30.0, vbox_vth=5.0,
+               steps=2000, precision=32, seed=2109067430) -> Config:
+    """Asymmetric current sheet: density ratio n1/n2 across y = 0, the hot
+    side 3x the temperature of the dense side, guide field bguide, Gaussian
+    X-line perturbation of strength xi and 1e-6 B0 noise on B_x (structure of
+    Sec. 4.1, not a run of the paper)."""
+    te2 = 0.5 / 6.0
+    # velocity boxes sized for the hot side
+    species = []
+    for name, q, m, t in (("e", -1.0, 1.0 / mass_ratio, te2 * t_ratio), ("i", 1.0, 1.0, 5 * te2 * t_ratio)):
+        vm = vbox_vth * math.sqrt(t / m)
+        species.append(SpeciesCfg(name, q, m, (nv, nv, nv), (-vm, -vm, -vm), (vm, vm, vm)))
+    dx, dy = lx / nx, ly / ny
+    cfg = Config("asym_2d3v_%dx%d_v%d" % (nx, ny, nv), 3, nx, ny, -lx / 2, lx, -ly / 2, ly, 1, species,
+                 0.5 * min(dx, dy) / c, steps, c=c, precision=precision)
+    cfg.lam, cfg.n_ratio, cfg.t_ratio, cfg.bguide, cfg.xi, cfg.seed, cfg.kind = (
+        lam, n_ratio, t_ratio, bguide, xi, seed, "asym")
+    return cfg
+
+
+# -------------------------------------------------------------- random data ---
+
+def random_blocks(shape, seed, low=0.0, high=1.0, dtype=np.float64):
+    """Positive random data for kernel tests."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(low, high, size=shape).astype(dtype)
+
+
+def random_fields(ncell, seed, e_scale=1.0, b_scale=1.0):
+    """Random cell-centred E and B [ncell][6]."""
+    rng = np.random.default_rng(seed)
+    eb = np.empty((ncell, 6))
+    eb[:, :3] = rng.normal(0.0, e_scale, size=(ncell, 3))
+    eb[:, 3:] = rng.normal(0.0, b_scale, size=(ncell, 3))
+    return eb
+
+
+# ------------------------------------------------------- smooth periodic wave ---
+
+def wave2d(nx=16, ny=8, nv=12, lx=6.4, ly=3.2, mass_ratio=25.0, amp=0.05, te=0.25, ti=0.25, bz=1.0,
+           c=10.0, vbox_vth=5.0, steps=20, precision=32) -> Config:
+    """Smooth periodic 2D3V test: quasi-neutral density wave n = 1 + amp
+    cos(2 pi x / lx) in both species, uniform temperatures, uniform B_z,
+    periodic in x and y (a well-resolved case for conservation checks)."""
+    species = []
+    for name, q, m, t in (("e", -1.0, 1.0 / mass_ratio, te), ("i", 1.0, 1.0, ti)):
+        vm = vbox_vth * math.sqrt(t / m)
+        species.append(SpeciesCfg(name, q, m, (nv, nv, nv), (-vm, -vm, -vm), (vm, vm, vm)))
+        species[-1].T = t
+    dx, dy = lx / nx, ly / ny
+    cfg = Config("wave_2d3v_%dx%d_v%d" % (nx, ny, nv), 3, nx, ny, 0.0, lx, 0.0, ly, 0, species,
+                 0.5 * min(dx, dy) / c, steps, c=c, precision=precision)
+    cfg.amp, cfg.bz, cfg.kind = amp, bz, "wave"
+    return cfg
+
+
+def wave2d_state(cfg: Config, dtype=np.float64):
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    n = 1.0 + cfg.amp * np.cos(2 * math.pi * x / cfg.lx)
+    out = []
+    for sp in cfg.species:
+        th = sp.T / sp.m
+        v = [sp.vcentres(a) for a in range(3)]
+        g = [np.exp(-va ** 2 / (2 * th)) for va in v]
+        blk = (g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :]) / (2 * math.pi * th) ** 1.5
+        f = n[None, :, None, None, None] * blk[None, None]
+        f = np.broadcast_to(f, (cfg.ny, cfg.nx) + blk.shape).astype(dtype)
+        out.append(np.ascontiguousarray(f))
+    return out
+
+
+def wave2d_yee(cfg: Config):
+    yee = np.zeros((6, cfg.ny + 1, cfg.nx))
+    yee[5, :cfg.ny, :] = cfg.bz
+    return yee
