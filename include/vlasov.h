@@ -1,0 +1,160 @@
+/*
+ * libvlasov -- GB300 (sm_103a) hot path of the moment-fitting PFC Vlasov
+ * solver of Allmann-Rahn, Lautenbach and Grauer, "An Energy Conserving Vlasov
+ * Solver That Tolerates Coarse Velocity Space Resolutions" (arXiv:2109.06743).
+ *
+ * C ABI. Plain pointers and sizes only. The library never allocates device
+ * memory: every buffer is owned by the caller (for example allocated with
+ * PyTorch) and must stay alive until vlasov_free. All compute calls are
+ * asynchronous on the given CUDA stream (NULL = legacy default stream) and
+ * return after enqueueing their kernels.
+ *
+ * Error behaviour: argument errors return VL_EINVAL immediately (nothing is
+ * enqueued) and vl_last_error() describes them; a failed kernel launch returns
+ * VL_ECUDA. Kernels that detect a problem on the device (non-finite or
+ * negative input moments, Newton fallbacks) count it in device-side counters
+ * read with vl_read_stats(); Newton non-convergence is not fatal: the
+ * continuous Maxwellian of the targets is used and counted.
+ *
+ * Layouts (row-major, fastest index last):
+ *   f_s        [ny][nx][nvz][nvy][nvx] of float (precision 32) or double (64);
+ *              1D1V: [nx][nv]. Velocity cell centres v_a(i) = vmin_a + (i+1/2) dv_a.
+ *   moments    [ny*nx][20] double: raw midpoint sums dv^3 sum_c v^alpha f_c for
+ *              alpha = 1, x, y, z, xx, xy, xz, yy, yz, zz, xxx, xxy, xxz, xyy,
+ *              xyz, xzz, yyy, yyz, yzz, zzz (1D1V: [nx][4] = 1, v, vv, vvv).
+ *   fluid      [nspecies][ny*nx][10] double: n, n u_a, int v_a v_b f dv
+ *              (= P/m) in the order xx, xy, xz, yy, yz, zz (1D1V: [..][3]).
+ *   yee        [6][ny+1][nx] double: Ex(i+1/2,j), Ey(i,j+1/2), Ez(i,j),
+ *              Bx(i,j+1/2), By(i+1/2,j), Bz(i+1/2,j+1/2); planes with a j+1/2
+ *              position use rows 0..ny-1 (2D3V only).
+ *   eb         [ny*nx][6] double: E and B at cell centres (written by
+ *              maxwell_step, read by pfc_advect_v and fluid_step).
+ *   theta      [ny*nx][10] double: n', u'_a, Theta'_ab (xx,xy,xz,yy,yz,zz) of a
+ *              fitted ten-moment Maxwellian (1D1V: [..][3]).
+ * Normalisation of the paper (Sec. 2.1): mu0 = k_B = 1, eps0 = 1/c^2;
+ * electrostatic 1D1V runs (Sec. 3.1) use eps0 = 1 and a Poisson solve.
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vl_stream_t; /* a cudaStream_t */
+typedef struct vl_ctx vl_ctx;             /* opaque, library-owned host object */
+
+typedef enum {
+    VL_OK = 0,
+    VL_EINVAL = 1,   /* invalid argument or descriptor                    */
+    VL_ECUDA = 2,    /* a CUDA call or kernel launch failed               */
+    VL_ENOCONV = 3,  /* (stats only) Newton fallback was used             */
+    VL_ENUMERIC = 4, /* (stats only) non-finite or negative input moments */
+    VL_ENOTSUP = 5   /* valid but unsupported shape (e.g. non-cubic block) */
+} vl_status;
+
+#define VL_MAX_SPECIES 4
+
+/* Problem descriptor (copied by vlasov_init). */
+typedef struct {
+    int nvdim;                      /* 1 (1D1V) or 3 (2D3V)                       */
+    int nx, ny;                     /* spatial cells (ny = 1 for 1D1V)            */
+    double x0, dx, y0, dy;          /* spatial cell edges and widths              */
+    int bc_y;                       /* 0 periodic in y, 1 conducting/reflecting walls */
+    int nspecies;                   /* 1..VL_MAX_SPECIES                          */
+    double q[VL_MAX_SPECIES];       /* charge                                     */
+    double m[VL_MAX_SPECIES];       /* mass                                       */
+    int nv[VL_MAX_SPECIES][3];      /* velocity cells per axis (cubic for 2D3V)   */
+    double vmin[VL_MAX_SPECIES][3]; /* velocity box, lower edge                   */
+    double vmax[VL_MAX_SPECIES][3]; /* velocity box, upper edge                   */
+    int precision;                  /* 32 or 64: element type of f                */
+    int nshear;                     /* 5: exact Boris factorisation, 3: plain split */
+    double c;                       /* speed of light (2D3V)                      */
+    double ion_background;          /* fixed neutralising density (1D1V)          */
+    double fit_tol;                 /* Newton tolerance relative to n (e.g. 1e-11) */
+    int fit_max_iter;               /* Newton iteration cap (e.g. 20)             */
+} vl_desc;
+
+/* Bytes of caller-provided device workspace that vlasov_init needs for this
+ * descriptor (shear tables, Newton parameters, fluid RK stages, counters).
+ * Returns 0 for an invalid descriptor. */
+size_t vlasov_work_bytes(const vl_desc* desc);
+
+/* Create a context. f_dev[s] is species s's distribution function (layout
+ * above, precision per desc), fluid_dev the fluid state, yee_dev the Yee
+ * fields (2D3V; may be NULL for 1D1V), eb_dev the cell-centred fields,
+ * work_dev/work_bytes the workspace (at least vlasov_work_bytes(desc), 256-byte
+ * aligned). All pointers are device pointers owned by the caller. Validates
+ * the descriptor (Sec. 3.3 walls need a velocity box symmetric in v_y). */
+vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev,
+                      double* yee_dev, double* eb_dev, void* work_dev,
+                      size_t work_bytes, vl_ctx** out);
+vl_status vlasov_free(vl_ctx* ctx);
+/* Human-readable description of the last error on this context (never NULL). */
+const char* vl_last_error(const vl_ctx* ctx);
+
+/* Spatial PFC sweep of species s along axis 0 (x, periodic) or 1 (y, periodic
+ * or reflecting walls with f(-y, v_y) = f(y, -v_y)), displacement v_a dt per
+ * velocity cell, in place. Paper Sec. 2.1 (PFC scheme of Filbet et al. 2001)
+ * and Sec. 3.3 (reflecting walls). |v| dt / dx may exceed 1. */
+vl_status pfc_advect_x(vl_ctx* ctx, int species, int axis, double dt, vl_stream_t stream);
+
+/* Velocity-space PFC advection of species s under (q/m)(E + v x B) over dt
+ * with the cell-centred fields eb, zero-flux at the velocity box (Sec. 2.1).
+ * 2D3V: the Boris map of each cell is factored into nshear single-axis
+ * shears, all applied to the block in shared memory. If mom_out is not NULL
+ * the raw moments of the advected f are written there ([ncell][20], fused
+ * epilogue, Sec. 2.1 moments). In place. */
+vl_status pfc_advect_v(vl_ctx* ctx, int species, double dt, double* mom_out,
+                       vl_stream_t stream);
+
+/* Raw midpoint moments of species s (Sec. 2.1), [ncell][20] (1D1V: [ncell][4]). */
+vl_status moments(vl_ctx* ctx, int species, double* mom_out, vl_stream_t stream);
+
+/* Moment fitting of Algorithm 1 (Sec. 2.2) for species s. vmom: raw moments
+ * of the current f ([ncell][20], e.g. from pfc_advect_v). The fluid moments
+ * of the context are rescaled by n_V/n_F; two discrete Maxwellians are fitted
+ * by FP64 Newton iteration (their midpoint moments of degree <= 2 equal the
+ * V and the rescaled F targets); then f <- f - f_M,V + f_M,F, negative values
+ * are clipped and the cell rescaled to n_V (limiter of Algorithm 1). The
+ * fluid state is replaced by its rescaled moments. use_mlp != 0 starts Newton
+ * from the trained network (mlp_set_weights) instead of the continuous
+ * Maxwellian. If theta_v/theta_f are not NULL the fitted parameters are
+ * written there. If mom_out is not NULL the raw moments of the new f are
+ * written there. In place on f and the fluid state. */
+vl_status moment_fit(vl_ctx* ctx, int species, const double* vmom, int use_mlp,
+                     double* theta_v, double* theta_f, double* mom_out,
+                     vl_stream_t stream);
+
+/* One SSP-RK3 step (Shu-Osher 1988) of the ten-moment equations of Sec. 2.1
+ * for every species with CWENO fluxes (Kurganov-Levy 2000). The third moments
+ * come from mom_t[s] (stage 1), mom_t1[s] (stage 2) and their average
+ * (stage 3), both raw moment arrays [ncell][20] (1D1V: [ncell][4]); E and B
+ * are the cell-centred fields of the context, frozen over the step. */
+vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t,
+                     const double* const* mom_t1, vl_stream_t stream);
+
+/* Field update. 2D3V: one leapfrog Yee step of length h (B h/2, E h, B h/2)
+ * with the current sum_s q_s n_s u_s taken from mom[s] (raw moments) or, if
+ * mom is NULL, from the fluid state; then the cell-centred eb. 1D1V: Poisson
+ * solve dE/dx = rho with rho = ion_background + sum_s q_s n_s (h unused).
+ * Paper Sec. 2.1 (FDTD, two half steps per time step) and Sec. 3.1. */
+vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom,
+                       vl_stream_t stream);
+
+/* Device counters accumulated since the last reset: out[0] Newton
+ * iterations, out[1] Newton fallbacks, out[2] clipped cells, out[3] cells
+ * with non-finite or non-positive targets. Synchronises the stream. */
+vl_status vl_read_stats(vl_ctx* ctx, long long out[4], vl_stream_t stream);
+vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream);
+
+/* Number of kernels this library has launched (all contexts, process-wide). */
+long long vl_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

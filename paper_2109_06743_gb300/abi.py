@@ -1,0 +1,198 @@
+"""ctypes binding of libvlasov.so (include/vlasov.h): argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels; this module converts
+Python arguments (torch tensors, integers) to the C ABI and raises
+``VlasovError`` on a non-zero status. There is no CPU fallback: ``lib()``
+raises if the shared library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvlasov.so")
+MAX_SPECIES = 4
+
+VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
+
+EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
+            "pfc_advect_v", "moments", "moment_fit", "fluid_step", "maxwell_step", "vl_read_stats",
+            "vl_reset_stats", "vl_launch_count"]
+
+
+class VlasovError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libvlasov status %d: %s" % (status, msg))
+        self.status = status
+
+
+class VlDesc(ctypes.Structure):
+    _fields_ = [
+        ("nvdim", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double),
+        ("dx", ctypes.c_double),
+        ("y0", ctypes.c_double),
+        ("dy", ctypes.c_double),
+        ("bc_y", ctypes.c_int),
+        ("nspecies", ctypes.c_int),
+        ("q", ctypes.c_double * MAX_SPECIES),
+        ("m", ctypes.c_double * MAX_SPECIES),
+        ("nv", (ctypes.c_int * 3) * MAX_SPECIES),
+        ("vmin", (ctypes.c_double * 3) * MAX_SPECIES),
+        ("vmax", (ctypes.c_double * 3) * MAX_SPECIES),
+        ("precision", ctypes.c_int),
+        ("nshear", ctypes.c_int),
+        ("c", ctypes.c_double),
+        ("ion_background", ctypes.c_double),
+        ("fit_tol", ctypes.c_double),
+        ("fit_max_iter", ctypes.c_int),
+    ]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_dpp = ctypes.POINTER(ctypes.c_void_p)
+
+
+def lib():
+    """Load libvlasov.so (raises if it is missing: no fallback path exists)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libvlasov.so not built: run paper_2109_06743_gb300.build.build() "
+                           "(or __graft_entry__.build()) first")
+    L = ctypes.CDLL(LIB_PATH)
+    D = ctypes.POINTER(VlDesc)
+    L.vlasov_work_bytes.argtypes = [D]
+    L.vlasov_work_bytes.restype = ctypes.c_size_t
+    L.vlasov_init.argtypes = [D, _dpp, _vp, _vp, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+    L.vlasov_free.argtypes = [_vp]
+    L.vl_last_error.argtypes = [_vp]
+    L.vl_last_error.restype = ctypes.c_char_p
+    L.pfc_advect_x.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp]
+    L.pfc_advect_v.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp]
+    L.moments.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+    L.moment_fit.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.fluid_step.argtypes = [_vp, ctypes.c_double, _dpp, _dpp, _vp]
+    L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
+    L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
+    L.vl_reset_stats.argtypes = [_vp, _vp]
+    L.vl_launch_count.argtypes = []
+    L.vl_launch_count.restype = ctypes.c_longlong
+    for name in EXPORTED:
+        getattr(L, name)
+        if name not in ("vlasov_work_bytes", "vl_last_error", "vl_launch_count"):
+            getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def ptr(x):
+    """Device (or host) address of a tensor, or an int/None passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_handle(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * MAX_SPECIES)()
+    for i, x in enumerate(xs):
+        arr[i] = ptr(x)
+    return arr
+
+
+def _check(ctx, st):
+    if st != VL_OK:
+        raise VlasovError(st, lib().vl_last_error(ctx).decode())
+
+
+def make_desc(cfg) -> VlDesc:
+    """vl_desc from a workloads.Config."""
+    d = VlDesc()
+    d.nvdim, d.nx, d.ny = cfg.nvdim, cfg.nx, cfg.ny
+    d.x0, d.dx, d.y0, d.dy = cfg.x0, cfg.dx, cfg.y0, cfg.dy
+    d.bc_y = cfg.bc_y
+    d.nspecies = len(cfg.species)
+    for s, sp in enumerate(cfg.species):
+        d.q[s], d.m[s] = sp.q, sp.m
+        for a in range(3):
+            d.nv[s][a] = sp.nv[a]
+            d.vmin[s][a] = sp.vmin[a]
+            d.vmax[s][a] = sp.vmax[a]
+    d.precision = cfg.precision
+    d.nshear = cfg.nshear
+    d.c = cfg.c or 0.0
+    d.ion_background = cfg.ion_background
+    d.fit_tol = cfg.fit_tol
+    d.fit_max_iter = cfg.fit_max_iter
+    return d
+
+
+def vlasov_work_bytes(desc: VlDesc) -> int:
+    return int(lib().vlasov_work_bytes(ctypes.byref(desc)))
+
+
+def vlasov_init(desc, f_list, fluid, yee, eb, work, work_bytes):
+    ctx = ctypes.c_void_p()
+    st = lib().vlasov_init(ctypes.byref(desc), _ptr_array(f_list), ptr(fluid), ptr(yee), ptr(eb), ptr(work),
+                           work_bytes, ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def vlasov_free(ctx):
+    lib().vlasov_free(ctx)
+
+
+def pfc_advect_x(ctx, species, axis, dt, stream=None):
+    _check(ctx, lib().pfc_advect_x(ctx, species, axis, dt, stream_handle(stream)))
+
+
+def pfc_advect_v(ctx, species, dt, mom_out=None, stream=None):
+    _check(ctx, lib().pfc_advect_v(ctx, species, dt, ptr(mom_out), stream_handle(stream)))
+
+
+def moments(ctx, species, mom_out, stream=None):
+    _check(ctx, lib().moments(ctx, species, ptr(mom_out), stream_handle(stream)))
+
+
+def moment_fit(ctx, species, vmom, use_mlp=False, theta_v=None, theta_f=None, mom_out=None, stream=None):
+    _check(ctx, lib().moment_fit(ctx, species, ptr(vmom), int(bool(use_mlp)), ptr(theta_v), ptr(theta_f),
+                                 ptr(mom_out), stream_handle(stream)))
+
+
+def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):
+    _check(ctx, lib().fluid_step(ctx, dt, _ptr_array(mom_t), _ptr_array(mom_t1), stream_handle(stream)))
+
+
+def maxwell_step(ctx, h, mom=None, stream=None):
+    arr = None if mom is None else _ptr_array(mom)
+    _check(ctx, lib().maxwell_step(ctx, h, arr, stream_handle(stream)))
+
+
+def vl_read_stats(ctx, stream=None):
+    out = (ctypes.c_longlong * 4)()
+    _check(ctx, lib().vl_read_stats(ctx, out, stream_handle(stream)))
+    return list(out)
+
+
+def vl_reset_stats(ctx, stream=None):
+    _check(ctx, lib().vl_reset_stats(ctx, stream_handle(stream)))
+
+
+def vl_launch_count():
+    return int(lib().vl_launch_count())

@@ -1,0 +1,427 @@
+// C-ABI layer of libvlasov: descriptor validation, workspace layout and the
+// entry points declared in include/vlasov.h. Every compute call only
+// enqueues kernels on the caller's stream.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct vl_ctx {
+    vl_desc d;
+    void* f[VL_MAX_SPECIES];
+    double* fluid;
+    double* yee;
+    double* eb;
+    vl::Workspace ws;
+    vl::MomConv conv[VL_MAX_SPECIES];
+    char err[512];
+};
+
+namespace vl {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n); }
+}  // namespace vl
+
+namespace {
+
+char g_err[512] = "";
+
+vl_status fail(vl_ctx* ctx, vl_status st, const char* fmt, ...) {
+    char* buf = ctx ? ctx->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+vl_status cuda_check(vl_ctx* ctx, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return VL_OK;
+    return fail(ctx, VL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+long long ncell_of(const vl_desc& d) { return (long long)d.nx * d.ny; }
+
+long long vblock_of(const vl_desc& d, int s) {
+    return d.nvdim == 1 ? d.nv[s][0] : (long long)d.nv[s][0] * d.nv[s][1] * d.nv[s][2];
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t shears, theta_v, theta_f, status, u1, u2, cur, counters, total;
+};
+
+Layout layout_of(const vl_desc& d) {
+    Layout L;
+    const size_t nc = (size_t)ncell_of(d);
+    size_t off = 0;
+    L.shears = off; off = align256(off + nc * 20 * sizeof(double));
+    L.theta_v = off; off = align256(off + nc * 10 * sizeof(double));
+    L.theta_f = off; off = align256(off + nc * 10 * sizeof(double));
+    L.status = off; off = align256(off + nc * 2 * sizeof(int));
+    L.u1 = off; off = align256(off + nc * 10 * sizeof(double));
+    L.u2 = off; off = align256(off + nc * 10 * sizeof(double));
+    L.cur = off; off = align256(off + nc * 3 * sizeof(double));
+    L.counters = off; off = align256(off + 4 * sizeof(unsigned long long));
+    L.total = off;
+    return L;
+}
+
+bool supported_block(int n) { return n == 8 || n == 12 || n == 16 || n == 20 || n == 24; }
+
+vl_status validate(const vl_desc* d, vl_ctx* ctx) {
+    if (!d) return fail(ctx, VL_EINVAL, "descriptor is NULL");
+    if (d->nvdim != 1 && d->nvdim != 3) return fail(ctx, VL_EINVAL, "nvdim must be 1 or 3 (got %d)", d->nvdim);
+    if (d->nx < 1 || d->ny < 1 || d->nx > 65535 || d->ny > 65535)
+        return fail(ctx, VL_EINVAL, "nx, ny must be in [1, 65535]");
+    if (d->nvdim == 1 && d->ny != 1) return fail(ctx, VL_EINVAL, "1D1V needs ny = 1");
+    if (!(d->dx > 0.0) || !(d->dy > 0.0)) return fail(ctx, VL_EINVAL, "dx, dy must be positive");
+    if (d->bc_y != 0 && d->bc_y != 1) return fail(ctx, VL_EINVAL, "bc_y must be 0 or 1");
+    if (d->bc_y == 1 && (d->nvdim != 3 || d->ny < 3)) return fail(ctx, VL_EINVAL, "walls in y need 2D3V and ny >= 3");
+    if (d->nspecies < 1 || d->nspecies > VL_MAX_SPECIES)
+        return fail(ctx, VL_EINVAL, "nspecies must be in [1, %d]", VL_MAX_SPECIES);
+    if (d->precision != 32 && d->precision != 64) return fail(ctx, VL_EINVAL, "precision must be 32 or 64");
+    if (d->nshear != 3 && d->nshear != 5) return fail(ctx, VL_EINVAL, "nshear must be 3 or 5");
+    if (!(d->fit_tol > 0.0) || d->fit_max_iter < 1 || d->fit_max_iter > 1000)
+        return fail(ctx, VL_EINVAL, "fit_tol must be > 0 and fit_max_iter in [1, 1000]");
+    if (d->nvdim == 3 && !(d->c > 0.0)) return fail(ctx, VL_EINVAL, "2D3V needs the speed of light c > 0");
+    for (int s = 0; s < d->nspecies; ++s) {
+        if (!(d->m[s] > 0.0) || !std::isfinite(d->q[s])) return fail(ctx, VL_EINVAL, "species %d: bad q or m", s);
+        int na = d->nvdim == 1 ? 1 : 3;
+        for (int a = 0; a < na; ++a) {
+            if (d->nv[s][a] < 1) return fail(ctx, VL_EINVAL, "species %d: nv must be positive", s);
+            if (!(d->vmax[s][a] > d->vmin[s][a])) return fail(ctx, VL_EINVAL, "species %d: vmax <= vmin", s);
+        }
+        if (d->nvdim == 1) {
+            if (d->nv[s][0] > 64) return fail(ctx, VL_ENOTSUP, "1D1V supports nv <= 64");
+        } else {
+            if (d->nv[s][0] != d->nv[s][1] || d->nv[s][0] != d->nv[s][2])
+                return fail(ctx, VL_ENOTSUP, "species %d: the velocity block must be cubic", s);
+            if (!supported_block(d->nv[s][0]))
+                return fail(ctx, VL_ENOTSUP, "species %d: nv = %d not compiled (8, 12, 16, 20, 24)", s, d->nv[s][0]);
+            if (d->bc_y == 1) {
+                double lo = d->vmin[s][1], hi = d->vmax[s][1];
+                if (std::fabs(lo + hi) > 1e-12 * (hi - lo))
+                    return fail(ctx, VL_EINVAL, "species %d: reflecting walls need a v_y box symmetric about 0", s);
+            }
+        }
+    }
+    return VL_OK;
+}
+
+double dv_of(const vl_desc& d, int s, int a) {
+    return (d.vmax[s][a] - d.vmin[s][a]) / d.nv[s][a];
+}
+
+void fill_box(const vl_desc& d, int s, double* vmin, double* dv) {
+    for (int a = 0; a < 3; ++a) {
+        bool used = d.nvdim == 3 || a == 0;
+        vmin[a] = used ? d.vmin[s][a] : 0.0;
+        dv[a] = used ? dv_of(d, s, a) : 1.0;
+    }
+}
+
+vl_status check_species(vl_ctx* ctx, int s) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species %d out of range", s);
+    return VL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vlasov_work_bytes(const vl_desc* desc) {
+    if (validate(desc, nullptr) != VL_OK) return 0;
+    return layout_of(*desc).total;
+}
+
+vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev, double* yee_dev, double* eb_dev,
+                      void* work_dev, size_t work_bytes, vl_ctx** out) {
+    if (!out) return fail(nullptr, VL_EINVAL, "out is NULL");
+    *out = nullptr;
+    vl_status st = validate(desc, nullptr);
+    if (st != VL_OK) return st;
+    if (!f_dev) return fail(nullptr, VL_EINVAL, "f_dev is NULL");
+    for (int s = 0; s < desc->nspecies; ++s)
+        if (!f_dev[s]) return fail(nullptr, VL_EINVAL, "f_dev[%d] is NULL", s);
+    if (!fluid_dev || !eb_dev) return fail(nullptr, VL_EINVAL, "fluid and eb buffers are required");
+    if (desc->nvdim == 3 && !yee_dev) return fail(nullptr, VL_EINVAL, "2D3V needs the Yee field buffer");
+    Layout L = layout_of(*desc);
+    if (!work_dev || work_bytes < L.total)
+        return fail(nullptr, VL_EINVAL, "workspace too small: %zu bytes given, %zu needed", work_bytes, L.total);
+    if (((uintptr_t)work_dev & 255u) != 0) return fail(nullptr, VL_EINVAL, "workspace must be 256-byte aligned");
+    vl_ctx* c = new vl_ctx();
+    c->d = *desc;
+    for (int s = 0; s < VL_MAX_SPECIES; ++s) c->f[s] = s < desc->nspecies ? f_dev[s] : nullptr;
+    c->fluid = fluid_dev;
+    c->yee = yee_dev;
+    c->eb = eb_dev;
+    char* w = static_cast<char*>(work_dev);
+    c->ws.shears = reinterpret_cast<double*>(w + L.shears);
+    c->ws.theta_v = reinterpret_cast<double*>(w + L.theta_v);
+    c->ws.theta_f = reinterpret_cast<double*>(w + L.theta_f);
+    c->ws.fit_status = reinterpret_cast<int*>(w + L.status);
+    c->ws.fluid_u1 = reinterpret_cast<double*>(w + L.u1);
+    c->ws.fluid_u2 = reinterpret_cast<double*>(w + L.u2);
+    c->ws.fluid_l = nullptr;
+    c->ws.cur = reinterpret_cast<double*>(w + L.cur);
+    c->ws.counters = reinterpret_cast<unsigned long long*>(w + L.counters);
+    c->ws.mlp = nullptr;
+    for (int s = 0; s < desc->nspecies; ++s) {
+        double vmin[3], dv[3];
+        fill_box(*desc, s, vmin, dv);
+        vl::make_mom_conv(vmin, dv, desc->nv[s][0], &c->conv[s]);
+    }
+    c->err[0] = 0;
+    cudaError_t e = cudaMemset(c->ws.counters, 0, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, VL_ECUDA, "clearing counters: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return VL_OK;
+}
+
+vl_status vlasov_free(vl_ctx* ctx) {
+    delete ctx;
+    return VL_OK;
+}
+
+const char* vl_last_error(const vl_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
+    if (st != VL_OK) return st;
+    const vl_desc& d = ctx->d;
+    if (axis != 0 && axis != 1) return fail(ctx, VL_EINVAL, "axis must be 0 or 1");
+    if (axis == 1 && d.nvdim != 3) return fail(ctx, VL_EINVAL, "1D1V has no y axis");
+    if (!std::isfinite(dt)) return fail(ctx, VL_EINVAL, "dt is not finite");
+    const long long V = vblock_of(d, s);
+    const int es = d.precision == 64 ? 8 : 4;
+    vl::SpaceSweepArgs a;
+    a.f = ctx->f[s];
+    a.V = V;
+    a.nvx = d.nv[s][0];
+    a.nvy = d.nvdim == 3 ? d.nv[s][1] : 1;
+    const int wall = axis == 1 && d.bc_y == 1;
+    a.wall = wall;
+    if (axis == 0) {
+        a.n = d.nx;
+        a.row_stride = V;
+        a.line_stride = (long long)d.nx * V;
+        a.nlines = d.ny;
+        a.axis_div = 1;
+        a.axis_mod = d.nv[s][0];
+        a.vmin_a = d.vmin[s][0];
+        a.dv_a = dv_of(d, s, 0);
+        a.dt_over_h = dt / d.dx;
+    } else {
+        a.n = d.ny;
+        a.row_stride = (long long)d.nx * V;
+        a.line_stride = V;
+        a.nlines = d.nx;
+        a.axis_div = d.nv[s][0];
+        a.axis_mod = d.nv[s][1];
+        a.vmin_a = d.vmin[s][1];
+        a.dv_a = dv_of(d, s, 1);
+        a.dt_over_h = dt / d.dy;
+    }
+    if (wall) {
+        double vmax = std::fmax(std::fabs(d.vmin[s][1]), std::fabs(d.vmax[s][1]));
+        int smax = (int)std::floor(vmax * std::fabs(dt) / d.dy);
+        if (d.ny < smax + 3) return fail(ctx, VL_EINVAL, "y sweep: |v_y| dt / dy too large for %d rows", d.ny);
+        a.mode = 1;
+        a.ncol = 2 * a.nvx;
+        a.nchunks = d.nv[s][2] * ((a.nvy + 1) / 2);
+    } else {
+        a.mode = 0;
+        a.ncol = 32;
+        while (a.ncol > 8 && (size_t)a.n * a.ncol * es > 96 * 1024) a.ncol /= 2;
+        a.nchunks = (int)((V + a.ncol - 1) / a.ncol);
+    }
+    if ((size_t)a.n * a.ncol * es > 200 * 1024 || a.ncol > 256)
+        return fail(ctx, VL_ENOTSUP, "spatial line too long for one shared-memory tile (%d cells)", a.n);
+    return cuda_check(ctx, vl::launch_pfc_space(a, d.precision, (cudaStream_t)stream), "pfc_advect_x");
+}
+
+vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
+    if (st != VL_OK) return st;
+    const vl_desc& d = ctx->d;
+    if (!std::isfinite(dt)) return fail(ctx, VL_EINVAL, "dt is not finite");
+    vl::VelocityArgs a;
+    a.f = ctx->f[s];
+    a.eb = ctx->eb;
+    a.shears = ctx->ws.shears;
+    a.mom_out = mom_out;
+    a.ncell = ncell_of(d);
+    a.nv = d.nv[s][0];
+    a.nshear = d.nshear;
+    a.qm = d.q[s] / d.m[s];
+    a.dt = dt;
+    fill_box(d, s, a.vmin, a.dv);
+    a.conv = ctx->conv[s];
+    return cuda_check(ctx, vl::launch_velocity(a, d.nvdim, d.precision, (cudaStream_t)stream), "pfc_advect_v");
+}
+
+vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
+    if (st != VL_OK) return st;
+    if (!mom_out) return fail(ctx, VL_EINVAL, "mom_out is NULL");
+    const vl_desc& d = ctx->d;
+    vl::MomentArgs a;
+    a.f = ctx->f[s];
+    a.mom_out = mom_out;
+    a.ncell = ncell_of(d);
+    a.nv = d.nv[s][0];
+    fill_box(d, s, a.vmin, a.dv);
+    a.conv = ctx->conv[s];
+    return cuda_check(ctx, vl::launch_moments(a, d.nvdim, d.precision, (cudaStream_t)stream), "moments");
+}
+
+vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
+                     double* mom_out, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
+    if (st != VL_OK) return st;
+    if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
+    if (use_mlp) return fail(ctx, VL_EINVAL, "no MLP weights have been set on this context");
+    const vl_desc& d = ctx->d;
+    const int ncomp = d.nvdim == 1 ? 3 : 10;
+    vl::FitArgs a;
+    a.vmom = vmom;
+    a.fluid = ctx->fluid + (size_t)s * ncell_of(d) * ncomp;
+    a.theta_v = theta_v ? theta_v : ctx->ws.theta_v;
+    a.theta_f = theta_f ? theta_f : ctx->ws.theta_f;
+    a.status = ctx->ws.fit_status;
+    a.counters = ctx->ws.counters;
+    a.mlp_w = nullptr;
+    a.ncell = ncell_of(d);
+    a.nv = d.nv[s][0];
+    fill_box(d, s, a.vmin, a.dv);
+    a.tol = d.fit_tol;
+    a.max_iter = d.fit_max_iter;
+    cudaStream_t cs = (cudaStream_t)stream;
+    st = cuda_check(ctx, vl::launch_fit(a, d.nvdim, cs), "moment_fit (Newton)");
+    if (st != VL_OK) return st;
+    vl::ExchangeArgs x;
+    x.f = ctx->f[s];
+    x.vmom = vmom;
+    x.theta_v = a.theta_v;
+    x.theta_f = a.theta_f;
+    x.status = a.status;
+    x.mom_out = mom_out;
+    x.counters = ctx->ws.counters;
+    x.ncell = a.ncell;
+    x.nv = a.nv;
+    for (int q = 0; q < 3; ++q) {
+        x.vmin[q] = a.vmin[q];
+        x.dv[q] = a.dv[q];
+    }
+    x.conv = ctx->conv[s];
+    return cuda_check(ctx, vl::launch_exchange(x, d.nvdim, d.precision, cs), "moment_fit (exchange)");
+}
+
+vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,
+                     vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    if (!mom_t || !mom_t1) return fail(ctx, VL_EINVAL, "moment arrays are NULL");
+    const vl_desc& d = ctx->d;
+    const int ncomp = d.nvdim == 1 ? 3 : 10;
+    const int nmom = d.nvdim == 1 ? 4 : 20;
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (int s = 0; s < d.nspecies; ++s) {
+        if (!mom_t[s] || !mom_t1[s]) return fail(ctx, VL_EINVAL, "moments of species %d are NULL", s);
+        double* U = ctx->fluid + (size_t)s * ncell_of(d) * ncomp;
+        vl::FluidArgs a;
+        a.U = U;
+        a.eb = ctx->eb;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.bc_y = d.bc_y;
+        a.nvdim = d.nvdim;
+        a.nmom = nmom;
+        a.dx = d.dx;
+        a.dy = d.dy;
+        a.qm = d.q[s] / d.m[s];
+        a.dt = dt;
+        a.q0 = mom_t[s];
+        a.q1 = mom_t1[s];
+        // stage 1: U1 = U + dt L(U; Q^t)
+        a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.wq0 = 1.0; a.wq1 = 0.0; a.a0 = 0.0; a.a1 = 1.0;
+        vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+        if (e != VL_OK) return e;
+        // stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1; Q^t+1))
+        a.Us = ctx->ws.fluid_u1; a.Uout = ctx->ws.fluid_u2; a.wq0 = 0.0; a.wq1 = 1.0; a.a0 = 0.75; a.a1 = 0.25;
+        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+        if (e != VL_OK) return e;
+        // stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2; Q^t+1/2))
+        a.Us = ctx->ws.fluid_u2; a.Uout = U; a.wq0 = 0.5; a.wq1 = 0.5; a.a0 = 1.0 / 3.0; a.a1 = 2.0 / 3.0;
+        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+        if (e != VL_OK) return e;
+    }
+    return VL_OK;
+}
+
+vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    const vl_desc& d = ctx->d;
+    const int ncomp = d.nvdim == 1 ? 3 : 10;
+    const int nmom = d.nvdim == 1 ? 4 : 20;
+    const long long nc = ncell_of(d);
+    const double* src[VL_MAX_SPECIES];
+    for (int s = 0; s < d.nspecies; ++s) {
+        if (mom && !mom[s]) return fail(ctx, VL_EINVAL, "moments of species %d are NULL", s);
+        src[s] = mom ? mom[s] : ctx->fluid + (size_t)s * nc * ncomp;
+    }
+    const int stride = mom ? nmom : ncomp;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (d.nvdim == 1) {
+        vl_status e = cuda_check(ctx, vl::launch_current(ctx->ws.cur, src, d.q, d.nspecies, stride, 0, nc, 1,
+                                                         d.ion_background, cs), "maxwell_step (charge)");
+        if (e != VL_OK) return e;
+        return cuda_check(ctx, vl::launch_poisson(ctx->ws.cur, ctx->eb, d.nx, d.dx, cs), "maxwell_step (Poisson)");
+    }
+    if (!std::isfinite(h)) return fail(ctx, VL_EINVAL, "h is not finite");
+    vl_status e = cuda_check(ctx, vl::launch_current(ctx->ws.cur, src, d.q, d.nspecies, stride, 1, nc, 3, 0.0, cs),
+                             "maxwell_step (current)");
+    if (e != VL_OK) return e;
+    vl::FieldArgs a;
+    a.yee = ctx->yee;
+    a.eb = ctx->eb;
+    a.cur = ctx->ws.cur;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.wall = d.bc_y == 1;
+    a.dx = d.dx;
+    a.dy = d.dy;
+    a.c2 = d.c * d.c;
+    a.h = h;
+    return cuda_check(ctx, vl::launch_maxwell(a, cs), "maxwell_step (FDTD)");
+}
+
+vl_status vl_read_stats(vl_ctx* ctx, long long out[4], vl_stream_t stream) {
+    if (!ctx || !out) return fail(ctx, VL_EINVAL, "NULL argument");
+    unsigned long long h[4];
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h, ctx->ws.counters, sizeof(h), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "vl_read_stats");
+    for (int q = 0; q < 4; ++q) out[q] = (long long)h[q];
+    return VL_OK;
+}
+
+vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    return cuda_check(ctx, cudaMemsetAsync(ctx->ws.counters, 0, 4 * sizeof(unsigned long long), (cudaStream_t)stream),
+                      "vl_reset_stats");
+}
+
+long long vl_launch_count(void) { return vl::g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Shared device-side definitions of libvlasov (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vlasov.h"
+
+namespace vl {
+
+constexpr int kMaxSpecies = VL_MAX_SPECIES;
+
+// Per-species constants passed by value to kernels.
+struct SpeciesParams {
+    double q, m, qm;
+    int nv[3];
+    double vmin[3], dv[3];
+    long long vblock;  // cells per velocity block
+};
+
+// Grid constants passed by value to kernels.
+struct GridParams {
+    int nvdim, nx, ny, bc_y;
+    double x0, dx, y0, dy;
+    long long ncell;
+};
+
+// Process-wide launch counter (reported by vl_launch_count).
+void count_launch(int n = 1);
+
+// Workspace layout offsets (bytes) computed by the ABI layer.
+struct Workspace {
+    double* shears;       // [ncell][5][4] shear factors of the velocity map
+    double* theta_v;      // [ncell][10]
+    double* theta_f;      // [ncell][10]
+    int* fit_status;      // [ncell][2] status of the V and F fits
+    double* fluid_u1;     // [ncell][10] RK stage 1 (per call, reused per species)
+    double* fluid_u2;     // [ncell][10]
+    double* fluid_l;      // [ncell][10]
+    double* cur;          // [ncell][3] current density at cell centres
+    unsigned long long* counters;  // [4]
+    float* mlp;           // MLP weights and scratch
+};
+
+__host__ __device__ inline int ifloor(double x) { return (int)floor(x); }
+
+}  // namespace vl

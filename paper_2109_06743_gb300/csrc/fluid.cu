@@ -1,0 +1,216 @@
+// Ten-moment fluid step (paper Sec. 2.1 equations with the third moment from
+// f, Sec. 2.2; CWENO of Kurganov and Levy 2000 and SSP-RK3 of Shu and Osher
+// 1988, cited in Sec. 2.1).
+//
+// Per species the state is U = (n, nu_a, E2_ab), E2 = P/m = int v v f. The
+// equations divided by m read
+//   dn/dt     + d_k nu_k    = 0
+//   dnu_a/dt  + d_k E2_ka   = (q/m) (n E_a + (nu x B)_a)
+//   dE2_ab/dt + d_k E3_kab  = (q/m) (nu_a E_b + nu_b E_a + C_ab + C_ba),
+// C_ab = ((row a of E2) x B)_b, E3 = int v v v f taken from the Vlasov solver
+// and reconstructed with the same CWENO polynomials as U. Fluxes are the
+// central-upwind (local Lax-Friedrichs) flux with the ten-moment wave speed
+// |u_d| + sqrt(3 Theta_dd) of the two neighbouring cells. One thread per cell
+// and stage; the step is O(N_x), negligible next to the phase-space passes.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace vl {
+
+__device__ __forceinline__ int s2(int a, int b) {
+    return a == 0 ? b : (a == 1 ? (b == 0 ? 1 : b + 2) : (b == 0 ? 2 : (b == 1 ? 4 : 5)));
+}
+
+// index of the symmetric triple in xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz
+__device__ __forceinline__ int s3(int a, int b, int c) {
+    int x = (a == 0) + (b == 0) + (c == 0), y = (a == 1) + (b == 1) + (c == 1);
+    // by number of x, then y
+    if (x == 3) return 0;
+    if (x == 2) return y == 1 ? 1 : 2;
+    if (x == 1) return y == 2 ? 3 : (y == 1 ? 4 : 5);
+    return y == 3 ? 6 : (y == 2 ? 7 : (y == 1 ? 8 : 9));
+}
+
+__device__ __forceinline__ void cweno3_point(double um, double u0, double up, double* left, double* right) {
+    const double eps = 1e-6;
+    double il = (u0 - um) * (u0 - um), ir = (up - u0) * (up - u0);
+    double d2 = up - 2.0 * u0 + um, d1 = up - um;
+    double ic = (13.0 / 3.0) * d2 * d2 + 0.25 * d1 * d1;
+    double al = 0.25 / ((eps + il) * (eps + il));
+    double ar = 0.25 / ((eps + ir) * (eps + ir));
+    double ac = 0.5 / ((eps + ic) * (eps + ic));
+    double sum = al + ar + ac;
+    double wl = al / sum, wr = ar / sum, wc = ac / sum;
+    // values at xi = -1/2 and +1/2 of the linear left/right and the central
+    // polynomial P_C = (P_opt - P_L/4 - P_R/4) / (1/2)
+    double base = u0 - d2 / 24.0 + 0.125 * d2;
+    double optl = base - 0.25 * d1, optr = base + 0.25 * d1;
+    double ll = u0 - 0.5 * (u0 - um), lr = u0 + 0.5 * (u0 - um);
+    double rl = u0 - 0.5 * (up - u0), rr = u0 + 0.5 * (up - u0);
+    double cl = 2.0 * optl - 0.5 * ll - 0.5 * rl;
+    double cr = 2.0 * optr - 0.5 * lr - 0.5 * rr;
+    *left = wl * ll + wr * rl + wc * cl;
+    *right = wl * lr + wr * rr + wc * cr;
+}
+
+struct FluidCtx {
+    const FluidArgs* a;
+    int nc, nq, qoff;
+};
+
+// sign of a component under y -> -y (v_y -> -v_y)
+__device__ __forceinline__ double parity_state(int k) {
+    // n nux nuy nuz xx xy xz yy yz zz
+    return (k == 2 || k == 5 || k == 8) ? -1.0 : 1.0;
+}
+__device__ __forceinline__ double parity_q(int k) {
+    // xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    return (k == 1 || k == 4 || k == 6 || k == 8) ? -1.0 : 1.0;
+}
+
+// resolve (ix, iy) with periodic x and periodic-or-wall y; returns the
+// linear cell index and the mirror flag
+__device__ __forceinline__ long long resolve(const FluidArgs& a, int ix, int iy, bool* mir) {
+    ix %= a.nx;
+    if (ix < 0) ix += a.nx;
+    *mir = false;
+    if (iy < 0 || iy >= a.ny) {
+        if (a.bc_y == 1) {
+            iy = iy < 0 ? -1 - iy : 2 * a.ny - 1 - iy;
+            *mir = true;
+        } else {
+            iy %= a.ny;
+            if (iy < 0) iy += a.ny;
+        }
+    }
+    return (long long)iy * a.nx + ix;
+}
+
+__device__ __forceinline__ double state_at(const FluidCtx& c, int k, int ix, int iy) {
+    bool mir;
+    long long id = resolve(*c.a, ix, iy, &mir);
+    double v = c.a->Us[id * c.nc + k];
+    return (mir && c.a->nvdim == 3) ? v * parity_state(k) : v;
+}
+
+__device__ __forceinline__ double q_at(const FluidCtx& c, int k, int ix, int iy) {
+    bool mir;
+    long long id = resolve(*c.a, ix, iy, &mir);
+    const FluidArgs& a = *c.a;
+    double v = 0.0;
+    if (a.wq0 != 0.0) v += a.wq0 * a.q0[id * a.nmom + c.qoff + k];
+    if (a.wq1 != 0.0) v += a.wq1 * a.q1[id * a.nmom + c.qoff + k];
+    return (mir && a.nvdim == 3) ? v * parity_q(k) : v;
+}
+
+__device__ __forceinline__ double wave_speed(int nvdim, int dir, const double* u) {
+    double n = u[0];
+    if (!(n > 0.0)) return 0.0;
+    double ud = u[1 + dir] / n;
+    double e2 = nvdim == 1 ? u[2] : u[4 + s2(dir, dir)];
+    double th = e2 / n - ud * ud;
+    if (th < 0.0) th = 0.0;
+    return fabs(ud) + sqrt(3.0 * th);
+}
+
+__device__ __forceinline__ double flux_of(int nvdim, int dir, int k, const double* u, const double* q) {
+    if (nvdim == 1) return k == 0 ? u[1] : (k == 1 ? u[2] : q[0]);
+    if (k == 0) return u[1 + dir];
+    if (k < 4) return u[4 + s2(dir, k - 1)];
+    const int ab[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    return q[s3(dir, ab[k - 4][0], ab[k - 4][1])];
+}
+
+// numerical flux through the interface between cell (lx, ly) and its
+// neighbour in direction dir
+__device__ void interface_flux(const FluidCtx& c, int dir, int lx, int ly, double* H) {
+    const int ox = dir == 0, oy = dir == 1;
+    double uL[10], uR[10], cL[10], cR[10], qL[10], qR[10];
+    for (int k = 0; k < c.nc; ++k) {
+        double a0 = state_at(c, k, lx - ox, ly - oy), a1 = state_at(c, k, lx, ly);
+        double a2 = state_at(c, k, lx + ox, ly + oy), a3 = state_at(c, k, lx + 2 * ox, ly + 2 * oy);
+        double l, r;
+        cweno3_point(a0, a1, a2, &l, &r);
+        uL[k] = r;
+        cweno3_point(a1, a2, a3, &l, &r);
+        uR[k] = l;
+        cL[k] = a1;
+        cR[k] = a2;
+    }
+    for (int k = 0; k < c.nq; ++k) {
+        double a0 = q_at(c, k, lx - ox, ly - oy), a1 = q_at(c, k, lx, ly);
+        double a2 = q_at(c, k, lx + ox, ly + oy), a3 = q_at(c, k, lx + 2 * ox, ly + 2 * oy);
+        double l, r;
+        cweno3_point(a0, a1, a2, &l, &r);
+        qL[k] = r;
+        cweno3_point(a1, a2, a3, &l, &r);
+        qR[k] = l;
+    }
+    const int nvdim = c.a->nvdim;
+    double sp = fmax(wave_speed(nvdim, dir, cL), wave_speed(nvdim, dir, cR));
+    for (int k = 0; k < c.nc; ++k)
+        H[k] = 0.5 * (flux_of(nvdim, dir, k, uL, qL) + flux_of(nvdim, dir, k, uR, qR)) - 0.5 * sp * (uR[k] - uL[k]);
+}
+
+__global__ void fluid_stage_kernel(FluidArgs a) {
+    long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= (long long)a.nx * a.ny) return;
+    const int ix = (int)(cell % a.nx), iy = (int)(cell / a.nx);
+    FluidCtx c;
+    c.a = &a;
+    c.nc = a.nvdim == 1 ? 3 : 10;
+    c.nq = a.nvdim == 1 ? 1 : 10;
+    c.qoff = a.nvdim == 1 ? 3 : 10;
+    double L[10];
+    for (int k = 0; k < c.nc; ++k) L[k] = 0.0;
+    const int ndir = a.nvdim == 1 ? 1 : 2;
+    double Hm[10], Hp[10];
+    for (int dir = 0; dir < ndir; ++dir) {
+        const double h = dir == 0 ? a.dx : a.dy;
+        interface_flux(c, dir, ix - (dir == 0), iy - (dir == 1), Hm);
+        interface_flux(c, dir, ix, iy, Hp);
+        // walls: the interface beyond the last row is the wall itself
+        // (mirror ghosts already give its flux); nothing special needed
+        for (int k = 0; k < c.nc; ++k) L[k] -= (Hp[k] - Hm[k]) / h;
+    }
+    const double* u = a.Us + cell * c.nc;
+    const double* eb = a.eb + cell * 6;
+    const double qm = a.qm;
+    if (a.nvdim == 1) {
+        L[1] += qm * u[0] * eb[0];
+        L[2] += qm * 2.0 * u[1] * eb[0];
+    } else {
+        const double* E = eb;
+        const double* B = eb + 3;
+        const double* nu = u + 1;
+        L[1] += qm * (u[0] * E[0] + nu[1] * B[2] - nu[2] * B[1]);
+        L[2] += qm * (u[0] * E[1] + nu[2] * B[0] - nu[0] * B[2]);
+        L[3] += qm * (u[0] * E[2] + nu[0] * B[1] - nu[1] * B[0]);
+        double M[3][3];
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) M[p][q] = u[4 + s2(p, q)];
+        double C[3][3];
+        for (int p = 0; p < 3; ++p) {
+            C[p][0] = M[p][1] * B[2] - M[p][2] * B[1];
+            C[p][1] = M[p][2] * B[0] - M[p][0] * B[2];
+            C[p][2] = M[p][0] * B[1] - M[p][1] * B[0];
+        }
+        for (int p = 0; p < 3; ++p)
+            for (int q = p; q < 3; ++q) L[4 + s2(p, q)] += qm * (nu[p] * E[q] + nu[q] * E[p] + C[p][q] + C[q][p]);
+    }
+    for (int k = 0; k < c.nc; ++k) {
+        double us = a.Us[cell * c.nc + k];
+        double u0 = a.a0 != 0.0 ? a.U0[cell * c.nc + k] : 0.0;
+        a.Uout[cell * c.nc + k] = a.a0 * u0 + a.a1 * (us + a.dt * L[k]);
+    }
+}
+
+cudaError_t launch_fluid_stage(const FluidArgs& a, cudaStream_t st) {
+    long long n = (long long)a.nx * a.ny;
+    int threads = 128;
+    fluid_stage_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace vl

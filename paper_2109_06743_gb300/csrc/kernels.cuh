@@ -1,0 +1,120 @@
+// Kernel argument structs and host-side launchers of libvlasov.
+#pragma once
+
+#include "common.cuh"
+
+namespace vl {
+
+// ---- spatial PFC sweep ----------------------------------------------------
+struct SpaceSweepArgs {
+    void* f;
+    int n;                  // cells along the sweep axis
+    long long row_stride;   // elements between neighbouring cells along the line
+    long long line_stride;  // elements between neighbouring lines (blockIdx.y)
+    int nlines;             // number of lines
+    long long V;            // velocity block size
+    int wall;               // reflecting walls (mirror rows use the v_y-mirrored column)
+    int ncol, nchunks;      // velocity columns per tile, tiles per line
+    int mode;               // 0: contiguous columns, 1: v_y mirror pairs
+    int nvx, nvy;
+    int axis_div, axis_mod; // velocity index of the sweep axis: (vi / div) % mod
+    double vmin_a, dv_a, dt_over_h;
+};
+cudaError_t launch_pfc_space(const SpaceSweepArgs& a, int precision, cudaStream_t st);
+
+// ---- velocity-space PFC pass (+ fused moments) -----------------------------
+// Centred-index moments -> physical raw moments: out[o] = sum_t coef[o][t] *
+// im[idx[o][t]], t < nterm[o] (binomial expansion of v = vc + dv xi, times dv^3).
+struct MomConv {
+    double coef[20][8];
+    unsigned char idx[20][8];
+    unsigned char nterm[20];
+};
+void make_mom_conv(const double* vmin, const double* dv, int n, MomConv* out);
+
+struct VelocityArgs {
+    void* f;
+    const double* eb;       // [ncell][6]
+    double* shears;         // [ncell][5][4] workspace
+    double* mom_out;        // [ncell][20] or null
+    long long ncell;
+    int nv;                 // cubic block edge (2D3V); 1D1V: line length
+    int nshear;
+    double qm, dt;
+    double vmin[3], dv[3];
+    MomConv conv;
+};
+cudaError_t launch_velocity(const VelocityArgs& a, int nvdim, int precision, cudaStream_t st);
+
+struct MomentArgs {
+    const void* f;
+    double* mom_out;
+    long long ncell;
+    int nv;
+    double vmin[3], dv[3];
+    MomConv conv;
+};
+cudaError_t launch_moments(const MomentArgs& a, int nvdim, int precision, cudaStream_t st);
+
+// ---- moment fitting ----------------------------------------------------------
+struct FitArgs {
+    const double* vmom;     // [ncell][nmom] raw moments of f
+    double* fluid;          // [ncell][ncomp] fluid state (rescaled in place)
+    double* theta_v;        // [ncell][10]
+    double* theta_f;        // [ncell][10]
+    int* status;            // [ncell][2]
+    unsigned long long* counters;
+    const float* mlp_w;     // MLP weights or null
+    long long ncell;
+    int nv;
+    double vmin[3], dv[3];
+    double tol;
+    int max_iter;
+};
+cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
+
+struct ExchangeArgs {
+    void* f;
+    const double* vmom;     // [ncell][nmom] (n_V)
+    const double* theta_v;
+    const double* theta_f;
+    const int* status;
+    double* mom_out;        // moments of the new f or null
+    unsigned long long* counters;
+    long long ncell;
+    int nv;
+    double vmin[3], dv[3];
+    MomConv conv;
+};
+cudaError_t launch_exchange(const ExchangeArgs& a, int nvdim, int precision, cudaStream_t st);
+
+// ---- fluid ---------------------------------------------------------------------
+struct FluidArgs {
+    double* U;              // [ncell][ncomp] state (updated by the last stage)
+    const double* Us;       // stage input
+    double* Uout;           // stage output
+    const double* U0;       // state at t (for the RK combination)
+    const double* q0;       // raw moments with the third moments at offset qoff
+    const double* q1;
+    double wq0, wq1;        // Q = wq0 * q0 + wq1 * q1
+    const double* eb;
+    int nx, ny, bc_y, nvdim, nmom;
+    double dx, dy, qm, dt;
+    double a0, a1;          // Uout = a0 * U0 + a1 * (Us + dt L(Us))
+};
+cudaError_t launch_fluid_stage(const FluidArgs& a, cudaStream_t st);
+
+// ---- fields --------------------------------------------------------------------
+struct FieldArgs {
+    double* yee;            // [6][ny+1][nx]
+    double* eb;             // [ncell][6]
+    const double* cur;      // [ncell][3]
+    int nx, ny, wall;
+    double dx, dy, c2, h;
+};
+cudaError_t launch_current(double* cur, const double* const* src, const double* q, int nspecies,
+                           int stride, int off, long long ncell, int nvdim, double bg, cudaStream_t st);
+cudaError_t launch_maxwell(const FieldArgs& a, cudaStream_t st);
+cudaError_t launch_poisson(const double* rho, double* eb, int nx, double dx, cudaStream_t st);
+
+}  // namespace vl

@@ -1,0 +1,525 @@
+// Velocity-space PFC advection under the Lorentz force (paper Sec. 2.1) and
+// the midpoint moments of f (Sec. 2.1), fused.
+//
+// Each spatial cell's velocity block (N^3 values) is staged in shared memory
+// once; all velocity sweeps run there, so the pass moves f through HBM once
+// (read + write). The velocity map of one time step is affine, V = R (v + h)
+// + h (the Boris map, R a rotation about B, h = (q/m) E dt / 2). The paper
+// splits it into 1D sweeps ("backsubstitution", not detailed in the paper);
+// here R is factored exactly into five single-axis shears (rows p, b, c, b,
+// p, with p the axis of the largest |B| component), each of which is a 1D
+// PFC advection with a displacement that is constant along its line. The
+// factors are computed per cell in FP64 by a small kernel, then the block
+// kernel applies them with zero-flux boundaries at the velocity box.
+//
+// Shared-memory layout of a block: element (i, j, k) (i = v_x index fastest)
+// at (k N + j)(N + 1) + i: x lines are padded to N+1 so that a warp walking
+// 32 different lines hits distinct banks.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace vl {
+
+// --------------------------------------------------------------- shear factors
+
+__device__ void cross3(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// out[k][4] = (axis, coefficient of the lower other axis, of the higher one,
+// constant): sweep k moves v_axis by c1 v_lo + c2 v_hi + c0.
+__device__ void velocity_shears(double qm, double dt, const double* E, const double* B, int nshear,
+                                double* out) {
+    if (nshear == 3) {
+        double w = qm * dt;
+        double tab[3][4] = {{0, w * B[2], -w * B[1], w * E[0]},
+                            {1, -w * B[2], w * B[0], w * E[1]},
+                            {2, w * B[1], -w * B[0], w * E[2]}};
+        for (int k = 0; k < 3; ++k)
+            for (int q = 0; q < 4; ++q) out[k * 4 + q] = tab[k][q];
+        return;
+    }
+    double t[3], s[3], tt = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        t[a] = 0.5 * qm * dt * B[a];
+        tt += t[a] * t[a];
+    }
+    for (int a = 0; a < 3; ++a) s[a] = 2.0 * t[a] / (1.0 + tt);
+    // D = R - I, column by column: (e + e x t) x s
+    double D[3][3];
+    for (int col = 0; col < 3; ++col) {
+        double e[3] = {0.0, 0.0, 0.0}, et[3], w[3], r[3];
+        e[col] = 1.0;
+        cross3(e, t, et);
+        for (int a = 0; a < 3; ++a) w[a] = e[a] + et[a];
+        cross3(w, s, r);
+        for (int a = 0; a < 3; ++a) D[a][col] = r[a];
+    }
+    double h[3], bt[3];
+    for (int a = 0; a < 3; ++a) h[a] = 0.5 * qm * dt * E[a];
+    for (int a = 0; a < 3; ++a) bt[a] = D[a][0] * h[0] + D[a][1] * h[1] + D[a][2] * h[2] + 2.0 * h[a];
+    // pivot axis: largest |B| component (first on ties)
+    int p = 0;
+    if (fabs(B[1]) > fabs(B[p])) p = 1;
+    if (fabs(B[2]) > fabs(B[p])) p = 2;
+    int perm[3] = {p, p == 0 ? 1 : 0, p == 2 ? 1 : 2};
+    double M[3][3], dd0, dd1;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[i][j] = D[perm[i]][perm[j]] + (i == j ? 1.0 : 0.0);
+    dd0 = D[perm[0]][perm[0]];
+    dd1 = D[perm[1]][perm[1]];
+    // op 1, row 0: least-norm combination of rows 1, 2 making M00 = 1
+    double a1 = 0.0, b1 = 0.0;
+    {
+        double den = M[1][0] * M[1][0] + M[2][0] * M[2][0];
+        if (den > 0.0) {
+            a1 = -dd0 * M[1][0] / den;
+            b1 = -dd0 * M[2][0] / den;
+        }
+        for (int col = 0; col < 3; ++col) M[0][col] += a1 * M[1][col] + b1 * M[2][col];
+        M[0][0] = 1.0;
+    }
+    // op 2, row 1: rows 0, 2 making M10 = 0, M11 = 1
+    double c2, d2;
+    {
+        double det = M[2][1] - M[2][0] * M[0][1];
+        double r0 = -M[1][0], r1 = -dd1;
+        if (det != 0.0) {
+            d2 = (r1 - M[0][1] * r0) / det;
+            c2 = r0 - d2 * M[2][0];
+        } else {
+            d2 = 0.0;
+            c2 = r0;
+        }
+        for (int col = 0; col < 3; ++col) M[1][col] += c2 * M[0][col] + d2 * M[2][col];
+        M[1][0] = 0.0;
+        M[1][1] = 1.0;
+    }
+    // op 3, row 2: rows 0, 1 clearing M20, M21
+    double e3 = -M[2][0];
+    double g3 = -M[2][1] - e3 * M[0][1];
+    for (int col = 0; col < 3; ++col) M[2][col] += e3 * M[0][col] + g3 * M[1][col];
+    // op 4, row 1: row 2 clearing M12
+    double c4 = -M[1][2];
+    for (int col = 0; col < 3; ++col) M[1][col] += c4 * M[2][col];
+    // op 5, row 0: rows 1, 2 clearing M01, M02
+    double a5 = -M[0][1], b5 = -M[0][2];
+
+    // sweeps in application order (inverse operations 5, 4, 3, 2, 1); per
+    // sweep: permuted row and coefficients on the permuted columns
+    double lin[5][3] = {{0.0, -a5, -b5}, {0.0, 0.0, -c4}, {-e3, -g3, 0.0}, {-c2, 0.0, -d2}, {0.0, -a1, -b1}};
+    int prow[5] = {0, 1, 2, 1, 0};
+    // constants (sweeps 2, 3, 4) reproduce the translation bt
+    double bp[3] = {bt[perm[0]], bt[perm[1]], bt[perm[2]]};
+    double k2 = bp[2];
+    double k3 = bp[1] + d2 * k2;
+    double k4 = bp[0] - (a1 * d2 - b1) * k2 + a1 * k3;
+    double cst[5] = {0.0, 0.0, k2, k3, k4};
+    for (int k = 0; k < 5; ++k) {
+        int r = prow[k];
+        int o1 = r == 0 ? 1 : 0, o2 = r == 2 ? 1 : 2;  // other permuted indices, o1 < o2
+        int ax = perm[r];
+        double cl = lin[k][o1], ch = lin[k][o2];
+        if (perm[o1] > perm[o2]) {  // order the coefficients by physical axis
+            double tmp = cl;
+            cl = ch;
+            ch = tmp;
+        }
+        out[k * 4 + 0] = ax;
+        out[k * 4 + 1] = cl;
+        out[k * 4 + 2] = ch;
+        out[k * 4 + 3] = cst[k];
+    }
+}
+
+__global__ void shear_setup_kernel(const double* eb, double* shears, long long ncell, double qm, double dt,
+                                   int nshear) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    velocity_shears(qm, dt, eb + c * 6, eb + c * 6 + 3, nshear, shears + c * 20);
+}
+
+// ------------------------------------------------------------- line update
+
+template <typename T>
+__device__ __forceinline__ T phi_lim(T alpha, T A, T B, T fm, T f0, T fp) {
+    T up = fmin(fp - f0, T(2) * f0);
+    T dn = fmax(f0 - fm, T(-2) * f0);
+    return alpha * (f0 + A * up + B * dn);
+}
+
+// Zero-flux PFC step of one line of N values held in registers, positive
+// displacement s + alpha in the frame where index q runs along `dir`.
+// Writes the new line through `put(position, value)` (positions in the same
+// frame). Everything that would leave through the far boundary piles up in
+// the last cell; cells the profile has left become zero.
+template <typename T, int N, typename Put>
+__device__ __forceinline__ void pfc_line_zero_flux(T (&r)[N], int s, T alpha, Put put) {
+    const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
+    const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+    T phi_prev = T(0), old_prev = T(0), acc = T(0), phi = T(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        T fp = q + 1 < N ? r[q + 1] : T(0);
+        phi = phi_lim<T>(alpha, A, B, old_prev, r[q], fp);
+        T g = r[q] - phi + phi_prev;
+        phi_prev = phi;
+        old_prev = r[q];
+        r[q] = g;
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        int p = q + s;
+        if (p < N - 1) put(p, r[q]);
+        else acc += r[q];
+    }
+    put(N - 1, acc + phi);
+#pragma unroll
+    for (int p = 0; p < N - 1; ++p)
+        if (p < s) put(p, T(0));
+}
+
+template <int N>
+__device__ __forceinline__ int padded(int i, int j, int k) {
+    return (k * N + j) * (N + 1) + i;
+}
+
+// Apply one shear (axis, coefficients in velocity units) to the block in smem.
+template <typename T, int N>
+__device__ void apply_shear(T* blk, const double* sh, const double* vmin, const double* dv) {
+    const int axis = (int)sh[0];
+    const int t = threadIdx.x;
+    if (t >= N * N) return;
+    const int lo = t % N, hi = t / N;  // indices of the lower and higher other axes
+    const int alo = axis == 0 ? 1 : 0, ahi = axis == 2 ? 1 : 2;
+    const T vlo = (T)(vmin[alo] + (lo + 0.5) * dv[alo]);
+    const T vhi = (T)(vmin[ahi] + (hi + 0.5) * dv[ahi]);
+    const T inv = (T)(1.0 / dv[axis]);
+    T c = ((T)sh[1] * vlo + (T)sh[2] * vhi + (T)sh[3]) * inv;
+    const bool fwd = c >= T(0);
+    T ca = fwd ? c : -c;
+    int s = (int)floor(ca);
+    T alpha = ca - (T)s;
+    if (s > N) s = N;
+    auto addr = [&](int pos) -> int {
+        if (axis == 0) return padded<N>(pos, lo, hi);
+        if (axis == 1) return padded<N>(lo, pos, hi);
+        return padded<N>(lo, hi, pos);
+    };
+    T r[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) r[q] = blk[addr(fwd ? q : N - 1 - q)];
+    pfc_line_zero_flux<T, N>(r, s, alpha, [&](int p, T v) { blk[addr(fwd ? p : N - 1 - p)] = v; });
+}
+
+// ---------------------------------------------------------------- moments
+
+// Raw moments of the block in smem (padded layout) reduced over the CTA.
+// Line sums over v_x use centred indices (exact in binary floating point);
+// the 20 per-line products are reduced with warp shuffles in T and across
+// warps in FP64 by lanes 0..19 of warp 0, which then expand them to physical
+// velocities with the precomputed binomial table (FP64).
+template <typename T, int N>
+__device__ __forceinline__ void line_products(T (&m)[20], T S0, T S1, T S2, T S3, int j, int k) {
+    const T c = T(0.5) * T(N - 1);
+    T e = T(j) - c, z = T(k) - c;
+    T e2 = e * e, z2 = z * z, ez = e * z;
+    // order: 1 x y z xx xy xz yy yz zz xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+    m[0] = S0; m[1] = S1; m[2] = e * S0; m[3] = z * S0;
+    m[4] = S2; m[5] = e * S1; m[6] = z * S1; m[7] = e2 * S0; m[8] = ez * S0; m[9] = z2 * S0;
+    m[10] = S3; m[11] = e * S2; m[12] = z * S2; m[13] = e2 * S1; m[14] = ez * S1; m[15] = z2 * S1;
+    m[16] = e2 * e * S0; m[17] = e2 * z * S0; m[18] = e * z2 * S0; m[19] = z2 * z * S0;
+}
+
+template <typename T>
+__device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* out, const MomConv& conv) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int a = 0; a < 20; ++a) {
+        T v = m[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        m[a] = v;
+    }
+    const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 20; ++a) red[warp * 20 + a] = (double)m[a];
+    __syncthreads();
+    double* im = red + 20 * 32;
+    if (t < 20) {
+        double sacc = 0.0;
+        for (int w = 0; w < nwarp; ++w) sacc += red[w * 20 + t];
+        im[t] = sacc;
+    }
+    __syncwarp();
+    if (t < 20) {
+        double acc = 0.0;
+        for (int q = 0; q < conv.nterm[t]; ++q) acc += conv.coef[t][q] * im[conv.idx[t][q]];
+        out[t] = acc;
+    }
+}
+
+template <typename T, int N>
+__device__ void block_moments(const T* blk, double* red, double* out, const MomConv& conv) {
+    const int t = threadIdx.x;
+    T m[20];
+#pragma unroll
+    for (int a = 0; a < 20; ++a) m[a] = T(0);
+    if (t < N * N) {
+        const int j = t % N, k = t / N;
+        const T c = T(0.5) * T(N - 1);
+        T S0 = 0, S1 = 0, S2 = 0, S3 = 0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            T v = blk[padded<N>(i, j, k)];
+            T xi = T(i) - c;
+            T v1 = v * xi, v2 = v1 * xi;
+            S0 += v;
+            S1 += v1;
+            S2 += v2;
+            S3 += v2 * xi;
+        }
+        line_products<T, N>(m, S0, S1, S2, S3, j, k);
+    }
+    reduce_moments<T>(m, red, out, conv);
+}
+
+void make_mom_conv(const double* vmin, const double* dv, int n, MomConv* out) {
+    static const int P[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1},
+                                 {0, 2, 0}, {0, 1, 1}, {0, 0, 2}, {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0},
+                                 {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+    static const double binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    double vc[3];
+    for (int a = 0; a < 3; ++a) vc[a] = vmin[a] + 0.5 * n * dv[a];
+    const double vol = dv[0] * dv[1] * dv[2];
+    auto ipow = [](double x, int k) {
+        double r = 1.0;
+        for (int q = 0; q < k; ++q) r *= x;
+        return r;
+    };
+    for (int o = 0; o < 20; ++o) {
+        int nt = 0;
+        for (int p = 0; p <= P[o][0]; ++p)
+            for (int q = 0; q <= P[o][1]; ++q)
+                for (int r = 0; r <= P[o][2]; ++r) {
+                    double w = binom[P[o][0]][p] * ipow(vc[0], P[o][0] - p) * ipow(dv[0], p) *
+                               binom[P[o][1]][q] * ipow(vc[1], P[o][1] - q) * ipow(dv[1], q) *
+                               binom[P[o][2]][r] * ipow(vc[2], P[o][2] - r) * ipow(dv[2], r) * vol;
+                    if (w == 0.0) continue;
+                    int idx = 0;
+                    for (int u = 0; u < 20; ++u)
+                        if (P[u][0] == p && P[u][1] == q && P[u][2] == r) idx = u;
+                    out->coef[o][nt] = w;
+                    out->idx[o][nt] = (unsigned char)idx;
+                    ++nt;
+                }
+        out->nterm[o] = (unsigned char)nt;
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+
+template <typename T, int N>
+__device__ __forceinline__ void load_block(T* blk, const T* src) {
+    constexpr int V = N * N * N;
+    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+        int i = e % N, jk = e / N;
+        blk[jk * (N + 1) + i] = src[e];
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void store_block(T* dst, const T* blk) {
+    constexpr int V = N * N * N;
+    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+        int i = e % N, jk = e / N;
+        dst[e] = blk[jk * (N + 1) + i];
+    }
+}
+
+template <typename T, int N>
+__global__ void velocity_kernel(VelocityArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* blk = reinterpret_cast<T*>(smem_raw);
+    double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * N * N * (N + 1));
+    double* sh = red + 20 * 32 + 20;
+    T* f = reinterpret_cast<T*>(a.f);
+    constexpr long long V = (long long)N * N * N;
+    for (long long cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
+        load_block<T, N>(blk, f + cell * V);
+        if (threadIdx.x < 20) sh[threadIdx.x] = a.shears[cell * 20 + threadIdx.x];
+        __syncthreads();
+        for (int k = 0; k < a.nshear; ++k) {
+            apply_shear<T, N>(blk, sh + 4 * k, a.vmin, a.dv);
+            __syncthreads();
+        }
+        if (a.mom_out) block_moments<T, N>(blk, red, a.mom_out + cell * 20, a.conv);
+        store_block<T, N>(f + cell * V, blk);
+        __syncthreads();
+    }
+}
+
+template <typename T, int N>
+__global__ void moments_kernel(MomentArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* blk = reinterpret_cast<T*>(smem_raw);
+    double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * N * N * (N + 1));
+    const T* f = reinterpret_cast<const T*>(a.f);
+    constexpr long long V = (long long)N * N * N;
+    for (long long cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
+        load_block<T, N>(blk, f + cell * V);
+        __syncthreads();
+        block_moments<T, N>(blk, red, a.mom_out + cell * 20, a.conv);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- 1D1V
+
+// One thread per spatial cell: zero-flux PFC step of the velocity line with
+// c = (q/m) E dt / dv, straight from global memory (1D1V lines are short).
+template <typename T>
+__global__ void velocity1d_kernel(VelocityArgs a) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= a.ncell) return;
+    T* f = reinterpret_cast<T*>(a.f) + c * a.nv;
+    const int n = a.nv;
+    double cc = a.qm * a.eb[c * 6] * a.dt / a.dv[0];
+    bool fwd = cc >= 0.0;
+    double ca = fwd ? cc : -cc;
+    int s = (int)floor(ca);
+    T alpha = (T)(ca - s);
+    const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
+    const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+    T g[64];
+    auto at = [&](int q) -> T { return (q < 0 || q >= n) ? T(0) : f[fwd ? q : n - 1 - q]; };
+    T phi_prev = T(0), phi = T(0);
+    for (int q = 0; q < n; ++q) {
+        phi = phi_lim<T>(alpha, A, B, at(q - 1), at(q), at(q + 1));
+        g[q] = at(q) - phi + phi_prev;
+        phi_prev = phi;
+    }
+    T acc = T(0);
+    for (int p = 0; p < n; ++p) {
+        int q = p - s;
+        T v = (q >= 0) ? g[q] : T(0);
+        if (p == n - 1) {
+            for (int qq = (q >= 0 ? q : 0); qq < n; ++qq) acc += g[qq];
+            v = acc + phi;
+        }
+        f[fwd ? p : n - 1 - p] = v;
+    }
+    if (a.mom_out) {
+        double m[4] = {0, 0, 0, 0};
+        for (int q = 0; q < n; ++q) {
+            double v = a.vmin[0] + (q + 0.5) * a.dv[0], x = (double)f[q];
+            m[0] += x; m[1] += v * x; m[2] += v * v * x; m[3] += v * v * v * x;
+        }
+        for (int p = 0; p < 4; ++p) a.mom_out[c * 4 + p] = m[p] * a.dv[0];
+    }
+}
+
+template <typename T>
+__global__ void moments1d_kernel(MomentArgs a) {
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= a.ncell) return;
+    const T* f = reinterpret_cast<const T*>(a.f) + c * a.nv;
+    double m[4] = {0, 0, 0, 0};
+    for (int q = 0; q < a.nv; ++q) {
+        double v = a.vmin[0] + (q + 0.5) * a.dv[0], x = (double)f[q];
+        m[0] += x; m[1] += v * x; m[2] += v * v * x; m[3] += v * v * v * x;
+    }
+    for (int p = 0; p < 4; ++p) a.mom_out[c * 4 + p] = m[p] * a.dv[0];
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int g_num_sms = 0;
+static int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+template <typename T, int N>
+static cudaError_t launch_velocity_n(const VelocityArgs& a, cudaStream_t st) {
+    const int threads = ((N * N + 31) / 32) * 32;
+    size_t smem = sizeof(T) * N * N * (N + 1) + sizeof(double) * (20 * 32 + 20 + 20);
+    cudaFuncSetAttribute(velocity_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<T, N>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > a.ncell) grid = a.ncell;
+    velocity_kernel<T, N><<<(unsigned)grid, threads, smem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t launch_moments_n(const MomentArgs& a, cudaStream_t st) {
+    const int threads = ((N * N + 31) / 32) * 32;
+    size_t smem = sizeof(T) * N * N * (N + 1) + sizeof(double) * (20 * 32 + 20);
+    cudaFuncSetAttribute(moments_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, moments_kernel<T, N>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > a.ncell) grid = a.ncell;
+    moments_kernel<T, N><<<(unsigned)grid, threads, smem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+#define VL_DISPATCH_N(FN, T, nv, ...)                \
+    switch (nv) {                                    \
+        case 8: return FN<T, 8>(__VA_ARGS__);        \
+        case 12: return FN<T, 12>(__VA_ARGS__);      \
+        case 16: return FN<T, 16>(__VA_ARGS__);      \
+        case 20: return FN<T, 20>(__VA_ARGS__);      \
+        case 24: return FN<T, 24>(__VA_ARGS__);      \
+        default: return cudaErrorInvalidValue;       \
+    }
+
+cudaError_t launch_velocity(const VelocityArgs& a, int nvdim, int precision, cudaStream_t st) {
+    if (nvdim == 1) {
+        int threads = 128;
+        unsigned grid = (unsigned)((a.ncell + threads - 1) / threads);
+        if (precision == 64) velocity1d_kernel<double><<<grid, threads, 0, st>>>(a);
+        else velocity1d_kernel<float><<<grid, threads, 0, st>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+    {
+        int threads = 128;
+        unsigned grid = (unsigned)((a.ncell + threads - 1) / threads);
+        shear_setup_kernel<<<grid, threads, 0, st>>>(a.eb, a.shears, a.ncell, a.qm, a.dt, a.nshear);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (precision == 64) { VL_DISPATCH_N(launch_velocity_n, double, a.nv, a, st); }
+    VL_DISPATCH_N(launch_velocity_n, float, a.nv, a, st);
+}
+
+cudaError_t launch_moments(const MomentArgs& a, int nvdim, int precision, cudaStream_t st) {
+    if (nvdim == 1) {
+        int threads = 128;
+        unsigned grid = (unsigned)((a.ncell + threads - 1) / threads);
+        if (precision == 64) moments1d_kernel<double><<<grid, threads, 0, st>>>(a);
+        else moments1d_kernel<float><<<grid, threads, 0, st>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+    if (precision == 64) { VL_DISPATCH_N(launch_moments_n, double, a.nv, a, st); }
+    VL_DISPATCH_N(launch_moments_n, float, a.nv, a, st);
+}
+
+}  // namespace vl

@@ -1,0 +1,151 @@
+"""Algorithm 1 of the paper (Sec. 2.2) driven through the C-ABI.
+
+``Simulation`` owns the device buffers (allocated with PyTorch: plumbing only)
+and enqueues one time step as a sequence of libvlasov calls on one CUDA
+stream, with no host synchronisation inside a step:
+
+2D3V (Lie splitting x, y, v):
+  1. maxwell_step(dt/2)            current of the fluid state
+  2. Q^t                           moments of f^t (from the previous exchange)
+  3. pfc_advect_x(x), pfc_advect_x(y), pfc_advect_v(+ moments -> Q^t+1, V targets)
+  4. fluid_step(dt, Q^t, Q^t+1)    SSP-RK3, Q^t+1/2 = average
+  5. moment_fit                    Newton fits, exchange, limiter (+ moments of the new f)
+  6. maxwell_step(dt/2)            current of the fitted moments
+1D1V (Strang x/2, v, x/2; Poisson instead of FDTD, Sec. 3.1): E from the
+density after the first half x sweep.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import abi
+
+
+class Simulation:
+    def __init__(self, cfg, f_list, fluid_list=None, yee=None, device="cuda", stream=None, fit=True):
+        import torch
+
+        self.torch = torch
+        self.cfg = cfg
+        self.dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.fit = fit
+        self.dtype = torch.float32 if cfg.precision == 32 else torch.float64
+        nvdim, nc = cfg.nvdim, cfg.ncell
+        self.nmom = 4 if nvdim == 1 else 20
+        self.ncomp = 3 if nvdim == 1 else 10
+        with torch.cuda.stream(self.stream):
+            self.f = []
+            for f in f_list:
+                t = torch.as_tensor(np.asarray(f)).reshape(nc, -1).to(device=self.dev, dtype=self.dtype)
+                self.f.append(t.contiguous())
+            self.fluid = torch.zeros((len(cfg.species), nc, self.ncomp), dtype=torch.float64, device=self.dev)
+            self.eb = torch.zeros((nc, 6), dtype=torch.float64, device=self.dev)
+            if nvdim == 3:
+                y = np.zeros((6, cfg.ny + 1, cfg.nx)) if yee is None else np.asarray(yee, dtype=np.float64)
+                self.yee = torch.as_tensor(y.reshape(-1)).to(self.dev).contiguous()
+            else:
+                self.yee = None
+            self.desc = abi.make_desc(cfg)
+            self.work_bytes = abi.vlasov_work_bytes(self.desc)
+            if self.work_bytes == 0:
+                raise abi.VlasovError(abi.VL_EINVAL, abi.lib().vl_last_error(None).decode())
+            self.work = torch.zeros(self.work_bytes + 256, dtype=torch.uint8, device=self.dev)
+            off = (-self.work.data_ptr()) % 256
+            self.work_ptr = self.work.data_ptr() + off
+            self.mom_t = [torch.zeros((nc, self.nmom), dtype=torch.float64, device=self.dev) for _ in cfg.species]
+            self.mom_t1 = [torch.zeros((nc, self.nmom), dtype=torch.float64, device=self.dev) for _ in cfg.species]
+            self.mom_tmp = [torch.zeros((nc, self.nmom), dtype=torch.float64, device=self.dev) for _ in cfg.species]
+        self.ctx = abi.vlasov_init(self.desc, self.f, self.fluid, self.yee, self.eb, self.work_ptr, self.work_bytes)
+        s = self.stream
+        for k in range(len(cfg.species)):
+            abi.moments(self.ctx, k, self.mom_t[k], s)
+        with torch.cuda.stream(s):
+            if fluid_list is None:
+                # the fluid starts from the moments of f, so both solvers agree
+                for k in range(len(cfg.species)):
+                    self.fluid[k].copy_(self.mom_t[k][:, :self.ncomp])
+            else:
+                for k, u in enumerate(fluid_list):
+                    self.fluid[k].copy_(torch.as_tensor(np.asarray(u).reshape(nc, self.ncomp)))
+        if nvdim == 3:
+            abi.maxwell_step(self.ctx, 0.0, None, s)  # cell-centred fields of the initial Yee fields
+        else:
+            abi.maxwell_step(self.ctx, 0.0, self.mom_t, s)
+        self.time = 0.0
+
+    def close(self):
+        if self.ctx is not None:
+            abi.vlasov_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- Algorithm 1 -----------------------------------------------------------
+    def step(self, dt=None, use_mlp=False):
+        cfg, ctx, s = self.cfg, self.ctx, self.stream
+        dt = cfg.dt if dt is None else dt
+        ns = len(cfg.species)
+        if cfg.nvdim == 1:
+            abi.maxwell_step(ctx, 0.5 * dt, self.mom_t, s)
+            for k in range(ns):
+                abi.pfc_advect_x(ctx, k, 0, 0.5 * dt, s)
+                abi.moments(ctx, k, self.mom_tmp[k], s)
+            abi.maxwell_step(ctx, 0.5 * dt, self.mom_tmp, s)
+            for k in range(ns):
+                abi.pfc_advect_v(ctx, k, dt, None, s)
+                abi.pfc_advect_x(ctx, k, 0, 0.5 * dt, s)
+                abi.moments(ctx, k, self.mom_t1[k], s)
+        else:
+            abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
+            for k in range(ns):
+                abi.pfc_advect_x(ctx, k, 0, dt, s)
+                abi.pfc_advect_x(ctx, k, 1, dt, s)
+                abi.pfc_advect_v(ctx, k, dt, self.mom_t1[k], s)
+        if self.fit:
+            abi.fluid_step(ctx, dt, self.mom_t, self.mom_t1, s)
+            for k in range(ns):
+                abi.moment_fit(ctx, k, self.mom_t1[k], use_mlp, None, None, self.mom_t[k], s)
+        else:
+            self.mom_t, self.mom_t1 = self.mom_t1, self.mom_t
+        if cfg.nvdim == 1:
+            abi.maxwell_step(ctx, 0.5 * dt, self.mom_t, s)
+        else:
+            abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
+        self.time += dt
+
+    # -- host-side views (diagnostics and tests) --------------------------------
+    def f_host(self, k):
+        return self.f[k].double().cpu().numpy()
+
+    def stats(self):
+        return abi.vl_read_stats(self.ctx, self.stream)
+
+    def energies(self):
+        """(kinetic+thermal per species, electric, magnetic) from the moments
+        of f at t and the fields, summed on the host (diagnostic only)."""
+        cfg = self.cfg
+        self.stream.synchronize()
+        area = cfg.dx * (cfg.dy if cfg.nvdim == 3 else 1.0)
+        kin = []
+        for sp, m in zip(cfg.species, self.mom_t):
+            m = m.cpu().numpy()
+            v2 = m[:, 2] if cfg.nvdim == 1 else m[:, 4] + m[:, 7] + m[:, 9]
+            kin.append(0.5 * sp.m * v2.sum() * area)
+        if cfg.nvdim == 1:
+            e = self.eb[:, 0].cpu().numpy()
+            return kin, 0.5 * (e ** 2).sum() * area, 0.0
+        y = self.yee.cpu().numpy().reshape(6, cfg.ny + 1, cfg.nx)
+        rows = slice(0, cfg.ny + 1) if cfg.bc_y == 1 else slice(0, cfg.ny)
+        eps0 = 1.0 / cfg.c ** 2
+        ee = 0.5 * eps0 * ((y[0, rows] ** 2).sum() + (y[1, :cfg.ny] ** 2).sum() + (y[2, rows] ** 2).sum()) * area
+        eb = 0.5 * ((y[3, :cfg.ny] ** 2).sum() + (y[4, rows] ** 2).sum() + (y[5, :cfg.ny] ** 2).sum()) * area
+        return kin, ee, eb
+
+    def total_energy(self):
+        kin, ee, eb = self.energies()
+        return sum(kin) + ee + eb

@@ -1,0 +1,350 @@
+"""GPU parity of every libvlasov entry point against the FP64 oracle, called
+through the C-ABI on the same seeded inputs (paper Sec. 2.1, 2.2, Algorithm 1).
+
+Tolerances (derived from the arithmetic, stated per test):
+* FP64 kernels: the same operations in a different order (and with fused
+  multiply-adds) -> differences of a few ulps per operation: 1e-12 relative
+  to max|f| (sweeps), 1e-10 after a Newton fit.
+* FP32 kernels: inputs are the same FP32 values on both sides; each PFC
+  sweep rounds every cell a handful of times -> 2e-6 max|f| per sweep,
+  1e-5 max|f| after the five velocity shears; moments within 1e-5 of the
+  absolute moment scale sum |v^alpha| f dv^3 (the tolerance of the
+  spec precision policy for moments in FP32 mode).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2109_06743_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2109_06743_gb300 import build
+    build.build()
+    return torch
+
+
+def small_harris(nx=20, ny=12, nv=8, precision=64, bc_y=1):
+    cfg = W.harris(nx=nx, ny=ny, nv=nv, lx=25.6 * nx / 128, ly=12.8 * ny / 64, precision=precision)
+    cfg.bc_y = bc_y
+    return cfg
+
+
+def oracle_grid(orc, cfg):
+    return orc.make_grid(cfg.nvdim, cfg.nx, cfg.ny, cfg.x0, cfg.dx, cfg.y0, cfg.dy, cfg.bc_y)
+
+
+def oracle_species(orc, sp):
+    return orc.make_species(sp.q, sp.m, sp.nv, sp.vmin, sp.vmax)
+
+
+def cast(f, precision):
+    return f.astype(np.float32).astype(np.float64) if precision == 32 else f
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("axis,bc_y", [(0, 1), (1, 1), (1, 0)])
+@pytest.mark.parametrize("cfl", [0.37, 2.3])
+def test_space_sweep(gpu, orc, precision, axis, bc_y, cfl):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(precision=precision, bc_y=bc_y)
+    f0 = [cast(W.random_blocks((cfg.ncell, 512), 100 + k) ** 3, precision) for k in range(2)]
+    r = AbiRunner(cfg, f0)
+    g = oracle_grid(orc, cfg)
+    h = cfg.dx if axis == 0 else cfg.dy
+    for k, sp in enumerate(cfg.species):
+        dt = cfl * h / abs(sp.vmin[axis])
+        abi.pfc_advect_x(r.ctx, k, axis, dt)
+        ref = f0[k].copy()
+        orc.advect_space(ref, g, oracle_species(orc, sp), axis, dt)
+        got = r.f_np(k)
+        tol = (1e-12 if precision == 64 else 2e-6) * ref.max()
+        assert np.abs(got - ref).max() <= tol, (k, np.abs(got - ref).max(), tol)
+        assert abs(got.sum() - f0[k].sum()) <= (1e-13 if precision == 64 else 1e-6) * f0[k].sum()
+    r.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nshear", [5, 3])
+@pytest.mark.parametrize("nv", [8, 12])
+def test_velocity_pass_and_fused_moments(gpu, orc, precision, nshear, nv):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=5, ny=4, nv=nv, precision=precision)
+    cfg.nshear = nshear
+    V = nv ** 3
+    f0 = [cast(W.random_blocks((cfg.ncell, V), 200 + k) ** 4, precision) for k in range(2)]
+    eb = W.random_fields(cfg.ncell, 7, e_scale=0.5, b_scale=1.0)
+    eb[0, 3:] = 0.0            # a cell without magnetic field
+    eb[1, 3:5] = 0.0           # field along z only
+    r = AbiRunner(cfg, f0, eb=eb)
+    g = oracle_grid(orc, cfg)
+    dt = 0.01
+    for k, sp in enumerate(cfg.species):
+        mom = r.mom()
+        abi.pfc_advect_v(r.ctx, k, dt, mom)
+        ref = f0[k].copy()
+        s = oracle_species(orc, sp)
+        orc.advect_velocity(ref, g, s, eb, dt, nshear)
+        got = r.f_np(k)
+        tol = (1e-12 if precision == 64 else 1e-5) * ref.max()
+        assert np.abs(got - ref).max() <= tol, (k, np.abs(got - ref).max(), tol)
+        np.testing.assert_allclose(got.sum(axis=1), f0[k].sum(axis=1), rtol=1e-13 if precision == 64 else 2e-6)
+        # fused moments of the advected f versus the oracle's moments of the GPU result
+        r.sync()
+        m_gpu = mom.cpu().numpy()
+        m_ref = orc.moments(np.ascontiguousarray(got), g, s)
+        scale = abs_moment_scale(got, sp)
+        assert np.all(np.abs(m_gpu - m_ref) <= (1e-12 if precision == 64 else 1e-5) * scale)
+    r.close()
+
+
+MONO = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
+        (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1),
+        (0, 1, 2), (0, 0, 3)]
+
+
+def abs_moment_scale(f, sp, g=None, orc=None):
+    """sum |v^alpha| |f| dv^3 per cell and moment: the scale of the moment
+    tolerance (odd moments of symmetric f are ~0)."""
+    n = sp.nv[0]
+    v = [np.abs(sp.vcentres(a)) for a in range(3)]
+    F = np.abs(f).reshape(-1, n, n, n)  # [cell][k][j][i]
+    out = np.empty((F.shape[0], 20))
+    vol = float(np.prod(sp.dv))
+    for o, (p, q, r) in enumerate(MONO):
+        w = (v[2][:, None, None] ** r) * (v[1][None, :, None] ** q) * (v[0][None, None, :] ** p)
+        out[:, o] = (F * w[None]).sum(axis=(1, 2, 3)) * vol
+    return np.maximum(out, 1e-300)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_moments_standalone(gpu, orc, precision):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=6, ny=5, nv=12, precision=precision)
+    f0 = [cast(W.random_blocks((cfg.ncell, 1728), 300 + k), precision) for k in range(2)]
+    r = AbiRunner(cfg, f0)
+    g = oracle_grid(orc, cfg)
+    for k, sp in enumerate(cfg.species):
+        mom = r.mom()
+        abi.moments(r.ctx, k, mom)
+        r.sync()
+        ref = orc.moments(f0[k], g, oracle_species(orc, sp))
+        scale = abs_moment_scale(f0[k], sp)
+        assert np.all(np.abs(mom.cpu().numpy() - ref) <= (1e-12 if precision == 64 else 1e-5) * scale)
+    r.close()
+
+
+def near_maxwellian_state(cfg, seed, pert=0.05):
+    fs = W.harris_state(cfg)
+    rng = np.random.default_rng(seed)
+    out = []
+    for f in fs:
+        f = f.reshape(cfg.ncell, -1)
+        out.append(np.ascontiguousarray(f * (1.0 + pert * rng.uniform(-1, 1, f.shape))))
+    return out
+
+
+def fluid_targets(cfg, orc, f_list, seed):
+    """fluid moments = moments of f with perturbed n, u, T (so the exchange
+    really changes f)"""
+    rng = np.random.default_rng(seed)
+    g = oracle_grid(orc, cfg)
+    out = []
+    for f, sp in zip(f_list, cfg.species):
+        m = orc.moments(f, g, oracle_species(orc, sp))
+        n = m[:, 0] * (1.0 + 0.01 * rng.uniform(-1, 1, cfg.ncell))
+        u = m[:, 1:4] / m[:, :1] + 0.05 * np.array(sp.dv)[None, :] * rng.uniform(-1, 1, (cfg.ncell, 3))
+        E2 = m[:, 4:10] / m[:, :1]
+        mu = m[:, 1:4] / m[:, :1]
+        thv = E2 - np.stack([mu[:, 0] ** 2, mu[:, 0] * mu[:, 1], mu[:, 0] * mu[:, 2], mu[:, 1] ** 2,
+                             mu[:, 1] * mu[:, 2], mu[:, 2] ** 2], axis=1)
+        thf = thv * (1.0 + 0.02 * rng.uniform(-1, 1, (cfg.ncell, 1)))
+        uu = np.stack([u[:, 0] ** 2, u[:, 0] * u[:, 1], u[:, 0] * u[:, 2], u[:, 1] ** 2, u[:, 1] * u[:, 2],
+                       u[:, 2] ** 2], axis=1)
+        U = np.concatenate([n[:, None], n[:, None] * u, n[:, None] * (thf + uu)], axis=1)
+        out.append(np.ascontiguousarray(U))
+    return out
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_moment_fit_matches_oracle(gpu, orc, precision):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=6, ny=6, nv=12, precision=precision)
+    cfg.fit_tol = 1e-12
+    f0 = [cast(f, precision) for f in near_maxwellian_state(cfg, 400)]
+    U0 = fluid_targets(cfg, orc, f0, 401)
+    r = AbiRunner(cfg, f0, fluid=np.stack(U0))
+    g = oracle_grid(orc, cfg)
+    for k, sp in enumerate(cfg.species):
+        s = oracle_species(orc, sp)
+        vmom = r.mom()
+        abi.moments(r.ctx, k, vmom)
+        thv = r.torch.zeros((cfg.ncell, 10), dtype=r.torch.float64, device=r.dev)
+        thf = r.torch.zeros_like(thv)
+        mout = r.mom()
+        abi.moment_fit(r.ctx, k, vmom, False, thv, thf, mout)
+        r.sync()
+        # oracle: same algorithm on the same inputs
+        ref_f = f0[k].copy()
+        ref_U = U0[k].copy()
+        st = orc.moment_fit(ref_f, g, s, ref_U, cfg.fit_tol, cfg.fit_max_iter)
+        got = r.f_np(k)
+        tol = (1e-10 if precision == 64 else 2e-5) * ref_f.max()
+        assert np.abs(got - ref_f).max() <= tol, (np.abs(got - ref_f).max(), tol)
+        np.testing.assert_allclose(r.fluid[k].cpu().numpy(), ref_U, rtol=1e-12 if precision == 64 else 1e-6)
+        # fitted parameters against the oracle's fit of the GPU's V targets
+        vm = vmom.cpu().numpy()
+        for c in range(0, cfg.ncell, 7):
+            th, it, stt = orc.maxent_fit(vm[c, :10], s, 3, cfg.fit_tol, cfg.fit_max_iter)
+            if stt == 0:
+                np.testing.assert_allclose(thv[c].cpu().numpy(), th, rtol=1e-8, atol=1e-12 * abs(th).max())
+        # moments after the exchange equal the (rescaled) fluid targets when nothing was clipped
+        stats = abi.vl_read_stats(r.ctx)
+        assert stats[1] == 0 and stats[3] == 0, stats
+        if st[2] == 0:
+            m_after = mout.cpu().numpy()
+            dv = sp.dv[0]
+            Uk = r.fluid[k].cpu().numpy()
+            sc = np.concatenate([Uk[:, :1], Uk[:, :1] * dv * np.ones((1, 3)), Uk[:, :1] * dv * dv * np.ones((1, 6))],
+                                axis=1) + np.abs(Uk)
+            assert np.all(np.abs(m_after[:, :10] - Uk) <= (1e-9 if precision == 64 else 2e-5) * sc)
+        abi.vl_reset_stats(r.ctx)
+    r.close()
+
+
+@pytest.mark.parametrize("bc_y", [1, 0])
+def test_fluid_step_matches_oracle(gpu, orc, bc_y):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=10, ny=8, nv=8, precision=64, bc_y=bc_y)
+    f0 = near_maxwellian_state(cfg, 500)
+    g = oracle_grid(orc, cfg)
+    U0 = fluid_targets(cfg, orc, f0, 501)
+    eb = W.random_fields(cfg.ncell, 502, 0.3, 1.0)
+    r = AbiRunner(cfg, f0, fluid=np.stack(U0), eb=eb)
+    rng = np.random.default_rng(503)
+    mt, mt1 = [], []
+    for k in range(2):
+        a = r.mom()
+        b = r.mom()
+        abi.moments(r.ctx, k, a)
+        r.sync()
+        b.copy_(a * (1.0 + 0.01 * r.torch.as_tensor(rng.uniform(-1, 1, a.shape), device=r.dev)))
+        mt.append(a)
+        mt1.append(b)
+    dt = cfg.dt * 5
+    abi.fluid_step(r.ctx, dt, mt, mt1)
+    r.sync()
+    for k, sp in enumerate(cfg.species):
+        Uref = U0[k].copy()
+        q0 = mt[k].cpu().numpy()[:, 10:20].copy()
+        q1 = mt1[k].cpu().numpy()[:, 10:20].copy()
+        orc.fluid_step(Uref, g, oracle_species(orc, sp), q0, 0.5 * (q0 + q1), q1, eb, dt)
+        np.testing.assert_allclose(r.fluid[k].cpu().numpy(), Uref, rtol=1e-11, atol=1e-13 * np.abs(Uref).max())
+    r.close()
+
+
+@pytest.mark.parametrize("bc_y", [1, 0])
+def test_maxwell_step_matches_oracle(gpu, orc, bc_y):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=12, ny=8, nv=8, precision=64, bc_y=bc_y)
+    f0 = near_maxwellian_state(cfg, 600)
+    g = oracle_grid(orc, cfg)
+    rng = np.random.default_rng(601)
+    yee = rng.normal(size=(6, cfg.ny + 1, cfg.nx))
+    if bc_y:
+        yee[[0, 2], 0] = 0.0
+        yee[[0, 2], cfg.ny] = 0.0
+    else:
+        yee[[0, 2, 4], cfg.ny] = yee[[0, 2, 4], 0]
+    yee[[1, 3, 5], cfg.ny] = 0.0
+    U0 = fluid_targets(cfg, orc, f0, 602)
+    r = AbiRunner(cfg, f0, fluid=np.stack(U0), yee=yee)
+    h = 0.5 * cfg.dt
+    abi.maxwell_step(r.ctx, h, None)
+    r.sync()
+    J = sum(sp.q * U[:, 1:4] for sp, U in zip(cfg.species, U0))
+    ref = np.ascontiguousarray(yee.reshape(-1)).copy()
+    orc.maxwell(ref, g, J, h, cfg.c)
+    np.testing.assert_allclose(r.yee.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(r.eb.cpu().numpy(), orc.fields_to_centres(ref, g), rtol=0,
+                               atol=1e-12 * np.abs(ref).max())
+    r.close()
+
+
+def test_poisson_and_1d_step_parts(gpu, orc):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = W.landau(nx=16, nv=32)
+    f0 = W.landau_state(cfg)
+    r = AbiRunner(cfg, f0)
+    mom = r.mom()
+    abi.moments(r.ctx, 0, mom)
+    abi.maxwell_step(r.ctx, 0.0, [mom])
+    r.sync()
+    g = orc.make_grid(1, cfg.nx, 1, cfg.x0, cfg.dx)
+    s = oracle_species(orc, cfg.species[0])
+    rho = 1.0 - orc.moments(f0[0], g, s)[:, 0]
+    np.testing.assert_allclose(r.eb[:, 0].cpu().numpy(), orc.poisson_1d(rho, cfg.dx), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(mom.cpu().numpy(), orc.moments(f0[0], g, s), rtol=1e-13, atol=1e-16)
+    # 1D velocity push with a strong field (CFL > 1)
+    eb = np.zeros((cfg.ncell, 6))
+    eb[:, 0] = np.linspace(-3, 3, cfg.ncell)
+    r.eb.copy_(r.torch.as_tensor(eb))
+    abi.pfc_advect_v(r.ctx, 0, 0.4, None)
+    ref = f0[0].copy()
+    orc.advect_velocity(ref, g, s, eb, 0.4, 5)
+    np.testing.assert_allclose(r.f_np(0), ref, rtol=0, atol=1e-14 * ref.max())
+    r.close()
+
+
+def test_invalid_arguments_are_rejected(gpu):
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=4, ny=4, nv=8)
+    r = AbiRunner(cfg, [np.zeros((16, 512))] * 2)
+    with pytest.raises(abi.VlasovError) as e:
+        abi.pfc_advect_x(r.ctx, 5, 0, 0.1)
+    assert e.value.status == abi.VL_EINVAL
+    with pytest.raises(abi.VlasovError):
+        abi.pfc_advect_x(r.ctx, 0, 2, 0.1)
+    with pytest.raises(abi.VlasovError):
+        abi.moments(r.ctx, 0, None)
+    with pytest.raises(abi.VlasovError):
+        abi.pfc_advect_x(r.ctx, 0, 1, 1e9)  # displacement longer than the wall-bounded line
+    bad = abi.make_desc(cfg)
+    bad.nv[0][1] = 9  # non-cubic block
+    assert abi.vlasov_work_bytes(bad) == 0
+    r.close()
+
+
+def test_empty_cells_are_left_alone(gpu, orc):
+    """Cells with f = 0 have no Maxwellian to fit (invalid targets): the
+    exchange must leave them at zero and count them, not produce NaN."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=4, ny=4, nv=8)
+    f0 = near_maxwellian_state(cfg, 700)
+    f0[0][3] = 0.0
+    U0 = np.stack(fluid_targets(cfg, orc, f0, 701))
+    r = AbiRunner(cfg, f0, fluid=U0)
+    vm = r.mom()
+    abi.moments(r.ctx, 0, vm)
+    abi.moment_fit(r.ctx, 0, vm, False, None, None, None)
+    got = r.f_np(0)
+    assert np.all(got[3] == 0.0) and np.all(np.isfinite(got))
+    st = abi.vl_read_stats(r.ctx)
+    assert st[3] >= 1
+    r.close()
