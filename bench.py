@@ -1,0 +1,346 @@
+"""Benchmark of the moment-fitting PFC Vlasov hot path (arXiv:2109.06743).
+
+One step = one full time step of Algorithm 1 (Sec. 2.2) over the whole
+workload: field half step, x and y PFC sweeps, velocity PFC pass with fused
+moments, SSP-RK3 ten-moment fluid step, Newton fits of the V and F
+Maxwellians, exchange + limiter with fused moments, field half step, for
+both species. Inputs are synthetic (seeded Harris sheet, paper Sec. 3.3
+structure) and resident in HBM when the timed region starts; f (4.3 GB at
+the default size) is far larger than the 129 MB L2, so no flush is needed.
+
+Metric: phase-space cell updates per second = (sum over species of
+spatial cells x velocity cells) x steps / time, over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (oracle/, the baseline of this
+project; the paper has no code) on a bounded sample of the same workload on
+the host cores. Under torchrun each rank runs an independent replica
+(replicas only: the method's spatial decomposition is not needed on one
+GPU), the slowest rank's time is used and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "phase-space cell updates/s per step (FP32+MLP vs FP64 GPU) and % HBM roofline"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    # name: (nx, ny, nv, lx, ly)  -- Harris sheet, both species
+    "harris_512x256_v16": (512, 256, 16, 25.6, 12.8),
+    "harris_128x64_v20": (128, 64, 20, 25.6, 12.8),
+}
+
+
+def make_cfg(name, precision=32):
+    from paper_2109_06743_gb300 import workloads as W
+    nx, ny, nv, lx, ly = WORKLOADS[name]
+    cfg = W.harris(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
+    return cfg
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps=1, sample=(32, 16)):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    a 32x16 spatial subdomain with the workload's dx, dv (both species),
+    one Algorithm 1 step per timed step, single-threaded."""
+    import numpy as np
+
+    from oracle.step import OracleState
+    from paper_2109_06743_gb300 import workloads as W
+    nx, ny = sample
+    cfg = W.harris(nx=nx, ny=ny, nv=16, lx=25.6 * nx / 512, ly=12.8 * ny / 256, precision=64)
+    st = OracleState(cfg, W.harris_state(cfg), None, W.harris_yee(cfg))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.step(cfg.dt)
+    el = time.perf_counter() - t0
+    cells = cfg.phase_cells() * steps
+    return {"value": cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle step(s) of the Harris sheet on a %dx%d x 16^3 subdomain (2 species, %d cells, "
+                      "same dx, dv, dt as the workload), FP64, one host core, %.1f s" % (
+                          steps, nx, ny, cfg.phase_cells(), el)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not needed
+    cb = cpu_baseline(steps=args.steps, sample=(16, 8))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": None,
+            "config": {"workload": args.workload + " (oracle sample: 16x8 spatial subdomain)"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="harris_512x256_v16", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form timed for comparison")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300 import build as B
+    from paper_2109_06743_gb300 import workloads as W
+    from paper_2109_06743_gb300.driver import Simulation
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    abi.lib()
+
+    cfg = make_cfg(args.workload, precision=32)
+    f0 = W.harris_state(cfg, dtype=np.float32)
+    sim = Simulation(cfg, f0, None, W.harris_yee(cfg), device="cuda:%d" % local)
+    stream = sim.stream
+    cells = cfg.phase_cells()
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        sim.step()
+    abi.vl_reset_stats(sim.ctx, stream)
+    barrier_sync()
+
+    # ---- timed region: K steps, CUDA events on the solver's stream ----------
+    phase_ms = {}
+    pending = []
+    cur = {"label": None, "ev": None}
+
+    def mark(label):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        if cur["label"] is not None:
+            pending.append((cur["label"], cur["ev"], ev))
+        cur["label"], cur["ev"] = label, ev
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = abi.vl_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        sim.step(mark=mark)
+    t_end.record(stream)
+    barrier_sync()
+    launches = abi.vl_launch_count() - launches0
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    count = {}
+    for label, e0, e1 in pending:
+        phase_ms[label] = phase_ms.get(label, 0.0) + e0.elapsed_time(e1)
+        count[label] = count.get(label, 0) + 1
+    stats = abi.vl_read_stats(sim.ctx, stream)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = cells * args.steps * world / elapsed
+
+    # ---- roofline of the dominant kernel --------------------------------------
+    peak, peak_kind = peaks()
+    per_launch_cells = cells // len(cfg.species)  # one species per launch
+    hbm_phases = {"x_sweep": 8, "y_sweep": 8, "v_pass": 8, "fit_exchange": 8}
+    dom = max(phase_ms, key=lambda k: phase_ms[k])
+    rows = {}
+    for ph, b in hbm_phases.items():
+        if ph in phase_ms:
+            avg_s = phase_ms[ph] / count[ph] / 1e3
+            rows[ph] = {"ms_per_launch": avg_s * 1e3, "GBps": b * per_launch_cells / avg_s / 1e9,
+                        "frac_of_%s_hbm" % peak_kind: b * per_launch_cells / avg_s / 1e9 / peak}
+    if dom in hbm_phases:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["GBps"], "peak": peak, "unit": "GB/s",
+                "frac": rows[dom]["GBps"] / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": 8 * per_launch_cells}
+    else:
+        # FP64 Newton fit: bounded by the FP64 pipe (measured 1.2 TFLOP/s on GB300)
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": 1.2, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "note": "FP64 Newton fit; see DESIGN.md for its operation count"}
+
+    # ---- end to end through the public API with host buffers ------------------
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
+        for h, f in zip(host, sim.f):
+            h.copy_(f)
+        barrier_sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 5))
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(ksteps):
+                for h, f in zip(host, sim.f):
+                    f.copy_(h, non_blocking=True)
+                sim.step()
+                for h, f in zip(host, sim.f):
+                    h.copy_(f, non_blocking=True)
+        e1.record(stream)
+        barrier_sync()
+        et = e0.elapsed_time(e1) / 1e3
+        if dist:
+            t = torch.tensor([et], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        nbytes = sum(f.numel() * f.element_size() for f in sim.f)
+        e2e = {"value": cells * ksteps * world / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ksteps}
+
+    fit_iters = stats[0] / max(1, 2 * cfg.ncell * len(cfg.species) * args.steps)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP64 GPU form of the same workload -------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        cfg64 = make_cfg(args.workload, precision=64)
+        s64 = Simulation(cfg64, W.harris_state(cfg64, dtype=np.float64), None, W.harris_yee(cfg64),
+                         device="cuda:%d" % local)
+        s64.step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s64.stream)
+        for _ in range(args.fp64_steps):
+            s64.step()
+        b.record(s64.stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        fp64 = {"value": cells * args.fp64_steps / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                "steps": args.fp64_steps, "note": "same workload with FP64 f and sweeps, single GPU"}
+        s64.close()
+
+    if rank != 0:
+        return 0
+    cb = None if args.no_cpu else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [cfg.nx, cfg.ny], "nv": cfg.species[0].nv[0],
+                   "species": len(cfg.species), "phase_cells_per_gpu": cells,
+                   "precision": "f32 f and sweeps; f64 moments, Newton fit, fluid, fields",
+                   "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
+                       sum(cfg.ncell * s.vblock for s in cfg.species) * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "phases_ms_per_step": {k: v / args.steps for k, v in sorted(phase_ms.items())},
+        "hbm_phases": rows,
+        "newton_iterations_per_fit": fit_iters, "newton_fallbacks": stats[1], "clipped_cells": stats[2],
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

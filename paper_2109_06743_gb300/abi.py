@@ -17,8 +17,8 @@ MAX_SPECIES = 4
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
-            "pfc_advect_v", "moments", "moment_fit", "fluid_step", "maxwell_step", "vl_read_stats",
-            "vl_reset_stats", "vl_launch_count"]
+            "pfc_advect_v", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
+            "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count"]
 
 
 class VlasovError(RuntimeError):
@@ -77,6 +77,8 @@ def lib():
     L.pfc_advect_v.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp]
     L.moments.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     L.moment_fit.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.moment_fit_solve.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]
+    L.moment_fit_exchange.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
     L.fluid_step.argtypes = [_vp, ctypes.c_double, _dpp, _dpp, _vp]
     L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
@@ -173,6 +175,16 @@ def moments(ctx, species, mom_out, stream=None):
 def moment_fit(ctx, species, vmom, use_mlp=False, theta_v=None, theta_f=None, mom_out=None, stream=None):
     _check(ctx, lib().moment_fit(ctx, species, ptr(vmom), int(bool(use_mlp)), ptr(theta_v), ptr(theta_f),
                                  ptr(mom_out), stream_handle(stream)))
+
+
+def moment_fit_solve(ctx, species, vmom, use_mlp=False, theta_v=None, theta_f=None, stream=None):
+    _check(ctx, lib().moment_fit_solve(ctx, species, ptr(vmom), int(bool(use_mlp)), ptr(theta_v), ptr(theta_f),
+                                       stream_handle(stream)))
+
+
+def moment_fit_exchange(ctx, species, vmom, theta_v=None, theta_f=None, mom_out=None, stream=None):
+    _check(ctx, lib().moment_fit_exchange(ctx, species, ptr(vmom), ptr(theta_v), ptr(theta_f), ptr(mom_out),
+                                          stream_handle(stream)))
 
 
 def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):

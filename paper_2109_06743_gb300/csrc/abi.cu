@@ -285,8 +285,8 @@ vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
     return cuda_check(ctx, vl::launch_moments(a, d.nvdim, d.precision, (cudaStream_t)stream), "moments");
 }
 
-vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
-                     double* mom_out, vl_stream_t stream) {
+vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
+                           vl_stream_t stream) {
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
@@ -306,25 +306,36 @@ vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double
     fill_box(d, s, a.vmin, a.dv);
     a.tol = d.fit_tol;
     a.max_iter = d.fit_max_iter;
-    cudaStream_t cs = (cudaStream_t)stream;
-    st = cuda_check(ctx, vl::launch_fit(a, d.nvdim, cs), "moment_fit (Newton)");
+    return cuda_check(ctx, vl::launch_fit(a, d.nvdim, (cudaStream_t)stream), "moment_fit (Newton)");
+}
+
+vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, const double* theta_v, const double* theta_f,
+                              double* mom_out, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
+    if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
+    const vl_desc& d = ctx->d;
     vl::ExchangeArgs x;
     x.f = ctx->f[s];
     x.vmom = vmom;
-    x.theta_v = a.theta_v;
-    x.theta_f = a.theta_f;
-    x.status = a.status;
+    x.theta_v = theta_v ? theta_v : ctx->ws.theta_v;
+    x.theta_f = theta_f ? theta_f : ctx->ws.theta_f;
+    x.status = ctx->ws.fit_status;
     x.mom_out = mom_out;
     x.counters = ctx->ws.counters;
-    x.ncell = a.ncell;
-    x.nv = a.nv;
-    for (int q = 0; q < 3; ++q) {
-        x.vmin[q] = a.vmin[q];
-        x.dv[q] = a.dv[q];
-    }
+    x.ncell = ncell_of(d);
+    x.nv = d.nv[s][0];
+    fill_box(d, s, x.vmin, x.dv);
     x.conv = ctx->conv[s];
-    return cuda_check(ctx, vl::launch_exchange(x, d.nvdim, d.precision, cs), "moment_fit (exchange)");
+    return cuda_check(ctx, vl::launch_exchange(x, d.nvdim, d.precision, (cudaStream_t)stream),
+                      "moment_fit (exchange)");
+}
+
+vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
+                     double* mom_out, vl_stream_t stream) {
+    vl_status st = moment_fit_solve(ctx, s, vmom, use_mlp, theta_v, theta_f, stream);
+    if (st != VL_OK) return st;
+    return moment_fit_exchange(ctx, s, vmom, theta_v, theta_f, mom_out, stream);
 }
 
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,

@@ -86,10 +86,14 @@ class Simulation:
             pass
 
     # -- Algorithm 1 -----------------------------------------------------------
-    def step(self, dt=None, use_mlp=False):
+    def step(self, dt=None, use_mlp=False, mark=None):
+        """One time step. ``mark(label)``, if given, is called before each
+        phase (the benchmark records a CUDA event there); it does not change
+        the work."""
         cfg, ctx, s = self.cfg, self.ctx, self.stream
         dt = cfg.dt if dt is None else dt
         ns = len(cfg.species)
+        mark = mark or (lambda label: None)
         if cfg.nvdim == 1:
             abi.maxwell_step(ctx, 0.5 * dt, self.mom_t, s)
             for k in range(ns):
@@ -101,21 +105,31 @@ class Simulation:
                 abi.pfc_advect_x(ctx, k, 0, 0.5 * dt, s)
                 abi.moments(ctx, k, self.mom_t1[k], s)
         else:
+            mark("maxwell")
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
             for k in range(ns):
+                mark("x_sweep")
                 abi.pfc_advect_x(ctx, k, 0, dt, s)
+                mark("y_sweep")
                 abi.pfc_advect_x(ctx, k, 1, dt, s)
+                mark("v_pass")
                 abi.pfc_advect_v(ctx, k, dt, self.mom_t1[k], s)
         if self.fit:
+            mark("fluid")
             abi.fluid_step(ctx, dt, self.mom_t, self.mom_t1, s)
             for k in range(ns):
-                abi.moment_fit(ctx, k, self.mom_t1[k], use_mlp, None, None, self.mom_t[k], s)
+                mark("fit_solve")
+                abi.moment_fit_solve(ctx, k, self.mom_t1[k], use_mlp, None, None, s)
+                mark("fit_exchange")
+                abi.moment_fit_exchange(ctx, k, self.mom_t1[k], None, None, self.mom_t[k], s)
         else:
             self.mom_t, self.mom_t1 = self.mom_t1, self.mom_t
+        mark("maxwell")
         if cfg.nvdim == 1:
             abi.maxwell_step(ctx, 0.5 * dt, self.mom_t, s)
         else:
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
+        mark(None)
         self.time += dt
 
     # -- host-side views (diagnostics and tests) --------------------------------
