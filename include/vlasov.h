@@ -130,14 +130,14 @@ vl_status moment_fit(vl_ctx* ctx, int species, const double* vmom, int use_mlp,
                      vl_stream_t stream);
 
 /* The two halves of moment_fit, for callers that schedule or time them
- * separately: moment_fit_solve runs the Newton fits (writes theta_v/theta_f,
- * or the context's workspace when NULL, and rescales the fluid state);
- * moment_fit_exchange then applies f <- f - f_M,V + f_M,F and the limiter
- * with the parameters of the preceding solve (same theta pointers). */
+ * separately: moment_fit_solve runs the Newton fits, keeps their
+ * coefficients in the context's workspace (and writes theta_v/theta_f if not
+ * NULL) and rescales the fluid state; moment_fit_exchange then applies
+ * f <- f - f_M,V + f_M,F and the limiter with the Maxwellians of the
+ * preceding solve of the same species. */
 vl_status moment_fit_solve(vl_ctx* ctx, int species, const double* vmom, int use_mlp,
                            double* theta_v, double* theta_f, vl_stream_t stream);
 vl_status moment_fit_exchange(vl_ctx* ctx, int species, const double* vmom,
-                              const double* theta_v, const double* theta_f,
                               double* mom_out, vl_stream_t stream);
 
 /* One SSP-RK3 step (Shu-Osher 1988) of the ten-moment equations of Sec. 2.1

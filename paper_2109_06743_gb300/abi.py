@@ -78,7 +78,7 @@ def lib():
     L.moments.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     L.moment_fit.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.moment_fit_solve.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]
-    L.moment_fit_exchange.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+    L.moment_fit_exchange.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
     L.fluid_step.argtypes = [_vp, ctypes.c_double, _dpp, _dpp, _vp]
     L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
@@ -182,9 +182,8 @@ def moment_fit_solve(ctx, species, vmom, use_mlp=False, theta_v=None, theta_f=No
                                        stream_handle(stream)))
 
 
-def moment_fit_exchange(ctx, species, vmom, theta_v=None, theta_f=None, mom_out=None, stream=None):
-    _check(ctx, lib().moment_fit_exchange(ctx, species, ptr(vmom), ptr(theta_v), ptr(theta_f), ptr(mom_out),
-                                          stream_handle(stream)))
+def moment_fit_exchange(ctx, species, vmom, mom_out=None, stream=None):
+    _check(ctx, lib().moment_fit_exchange(ctx, species, ptr(vmom), ptr(mom_out), stream_handle(stream)))
 
 
 def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):

@@ -53,7 +53,7 @@ long long vblock_of(const vl_desc& d, int s) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t shears, theta_v, theta_f, status, u1, u2, cur, counters, total;
+    size_t shears, coef_v, coef_f, status, u1, u2, cur, counters, total;
 };
 
 Layout layout_of(const vl_desc& d) {
@@ -61,8 +61,8 @@ Layout layout_of(const vl_desc& d) {
     const size_t nc = (size_t)ncell_of(d);
     size_t off = 0;
     L.shears = off; off = align256(off + nc * 20 * sizeof(double));
-    L.theta_v = off; off = align256(off + nc * 10 * sizeof(double));
-    L.theta_f = off; off = align256(off + nc * 10 * sizeof(double));
+    L.coef_v = off; off = align256(off + nc * 16 * sizeof(double));
+    L.coef_f = off; off = align256(off + nc * 16 * sizeof(double));
     L.status = off; off = align256(off + nc * 2 * sizeof(int));
     L.u1 = off; off = align256(off + nc * 10 * sizeof(double));
     L.u2 = off; off = align256(off + nc * 10 * sizeof(double));
@@ -164,8 +164,8 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     c->eb = eb_dev;
     char* w = static_cast<char*>(work_dev);
     c->ws.shears = reinterpret_cast<double*>(w + L.shears);
-    c->ws.theta_v = reinterpret_cast<double*>(w + L.theta_v);
-    c->ws.theta_f = reinterpret_cast<double*>(w + L.theta_f);
+    c->ws.coef_v = reinterpret_cast<double*>(w + L.coef_v);
+    c->ws.coef_f = reinterpret_cast<double*>(w + L.coef_f);
     c->ws.fit_status = reinterpret_cast<int*>(w + L.status);
     c->ws.fluid_u1 = reinterpret_cast<double*>(w + L.u1);
     c->ws.fluid_u2 = reinterpret_cast<double*>(w + L.u2);
@@ -232,10 +232,16 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
         a.dv_a = dv_of(d, s, 1);
         a.dt_over_h = dt / d.dy;
     }
+    // largest displacement in cells, checked in floating point (no int overflow)
+    {
+        int ax = axis;
+        double vmax = std::fmax(std::fabs(d.vmin[s][ax]), std::fabs(d.vmax[s][ax]));
+        double dmax = vmax * std::fabs(dt) / (ax == 0 ? d.dx : d.dy);
+        if (!(dmax < 1.0e6)) return fail(ctx, VL_EINVAL, "displacement of %g cells is not supported", dmax);
+        if (wall && !(dmax + 3.0 <= (double)d.ny))
+            return fail(ctx, VL_EINVAL, "y sweep: |v_y| dt / dy = %g too large for %d rows between walls", dmax, d.ny);
+    }
     if (wall) {
-        double vmax = std::fmax(std::fabs(d.vmin[s][1]), std::fabs(d.vmax[s][1]));
-        int smax = (int)std::floor(vmax * std::fabs(dt) / d.dy);
-        if (d.ny < smax + 3) return fail(ctx, VL_EINVAL, "y sweep: |v_y| dt / dy too large for %d rows", d.ny);
         a.mode = 1;
         a.ncol = 2 * a.nvx;
         a.nchunks = d.nv[s][2] * ((a.nvy + 1) / 2);
@@ -296,8 +302,8 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     vl::FitArgs a;
     a.vmom = vmom;
     a.fluid = ctx->fluid + (size_t)s * ncell_of(d) * ncomp;
-    a.theta_v = theta_v ? theta_v : ctx->ws.theta_v;
-    a.theta_f = theta_f ? theta_f : ctx->ws.theta_f;
+    a.coef_v = ctx->ws.coef_v;
+    a.coef_f = ctx->ws.coef_f;
     a.status = ctx->ws.fit_status;
     a.counters = ctx->ws.counters;
     a.mlp_w = nullptr;
@@ -306,11 +312,18 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     fill_box(d, s, a.vmin, a.dv);
     a.tol = d.fit_tol;
     a.max_iter = d.fit_max_iter;
-    return cuda_check(ctx, vl::launch_fit(a, d.nvdim, (cudaStream_t)stream), "moment_fit (Newton)");
+    cudaStream_t cs = (cudaStream_t)stream;
+    st = cuda_check(ctx, vl::launch_fit(a, d.nvdim, cs), "moment_fit (Newton)");
+    if (st != VL_OK) return st;
+    if (theta_v) {
+        st = cuda_check(ctx, vl::launch_theta(a.coef_v, a.status, 0, theta_v, a.ncell, d.nvdim, cs), "theta");
+        if (st != VL_OK) return st;
+    }
+    if (theta_f) st = cuda_check(ctx, vl::launch_theta(a.coef_f, a.status, 1, theta_f, a.ncell, d.nvdim, cs), "theta");
+    return st;
 }
 
-vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, const double* theta_v, const double* theta_f,
-                              double* mom_out, vl_stream_t stream) {
+vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, double* mom_out, vl_stream_t stream) {
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
@@ -318,8 +331,8 @@ vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, const doub
     vl::ExchangeArgs x;
     x.f = ctx->f[s];
     x.vmom = vmom;
-    x.theta_v = theta_v ? theta_v : ctx->ws.theta_v;
-    x.theta_f = theta_f ? theta_f : ctx->ws.theta_f;
+    x.coef_v = ctx->ws.coef_v;
+    x.coef_f = ctx->ws.coef_f;
     x.status = ctx->ws.fit_status;
     x.mom_out = mom_out;
     x.counters = ctx->ws.counters;
@@ -335,7 +348,7 @@ vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double
                      double* mom_out, vl_stream_t stream) {
     vl_status st = moment_fit_solve(ctx, s, vmom, use_mlp, theta_v, theta_f, stream);
     if (st != VL_OK) return st;
-    return moment_fit_exchange(ctx, s, vmom, theta_v, theta_f, mom_out, stream);
+    return moment_fit_exchange(ctx, s, vmom, mom_out, stream);
 }
 
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,

@@ -31,8 +31,8 @@ void count_launch(int n = 1);
 // Workspace layout offsets (bytes) computed by the ABI layer.
 struct Workspace {
     double* shears;       // [ncell][5][4] shear factors of the velocity map
-    double* theta_v;      // [ncell][10]
-    double* theta_f;      // [ncell][10]
+    double* coef_v;       // [ncell][16] fit coefficients of f_M,V
+    double* coef_f;       // [ncell][16] fit coefficients of f_M,F
     int* fit_status;      // [ncell][2] status of the V and F fits
     double* fluid_u1;     // [ncell][10] RK stage 1 (per call, reused per species)
     double* fluid_u2;     // [ncell][10]

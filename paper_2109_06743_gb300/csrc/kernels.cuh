@@ -60,8 +60,8 @@ cudaError_t launch_moments(const MomentArgs& a, int nvdim, int precision, cudaSt
 struct FitArgs {
     const double* vmom;     // [ncell][nmom] raw moments of f
     double* fluid;          // [ncell][ncomp] fluid state (rescaled in place)
-    double* theta_v;        // [ncell][10]
-    double* theta_f;        // [ncell][10]
+    double* coef_v;         // [ncell][16] fit coefficients (eta, u0, sigma) of f_M,V
+    double* coef_f;         // [ncell][16] of f_M,F
     int* status;            // [ncell][2]
     unsigned long long* counters;
     const float* mlp_w;     // MLP weights or null
@@ -72,12 +72,14 @@ struct FitArgs {
     int max_iter;
 };
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
+cudaError_t launch_theta(const double* coef, const int* status, int which, double* theta, long long ncell, int nvdim,
+                         cudaStream_t st);
 
 struct ExchangeArgs {
     void* f;
     const double* vmom;     // [ncell][nmom] (n_V)
-    const double* theta_v;
-    const double* theta_f;
+    const double* coef_v;
+    const double* coef_f;
     const int* status;
     double* mom_out;        // moments of the new f or null
     unsigned long long* counters;

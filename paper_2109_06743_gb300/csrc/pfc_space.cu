@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(256) pfc_space_kernel(SpaceSweepArgs a) {
     double c = (a.vmin_a + (ia + 0.5) * a.dv_a) * a.dt_over_h;
     const bool fwd = c >= 0.0;
     double ca = fwd ? c : -c;
+    // periodic lines: a shift by whole line lengths is the identity; walls:
+    // the host guarantees ca + 3 <= n. Clamp before the int conversion.
+    if (!a.wall) ca = fmod(ca, (double)n);
+    if (!(ca <= (double)n)) ca = (double)n;
     const int s = (int)floor(ca);
     const T alpha = (T)(ca - s);
     const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);

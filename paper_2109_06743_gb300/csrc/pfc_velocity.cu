@@ -200,9 +200,11 @@ __device__ void apply_shear(T* blk, const double* sh, const double* vmin, const 
     T c = ((T)sh[1] * vlo + (T)sh[2] * vhi + (T)sh[3]) * inv;
     const bool fwd = c >= T(0);
     T ca = fwd ? c : -c;
+    // beyond N cells everything piles up in the last cell anyway; clamping in
+    // floating point also maps NaN to N, so the int conversion is always safe
+    if (!(ca < T(N))) ca = T(N);
     int s = (int)floor(ca);
     T alpha = ca - (T)s;
-    if (s > N) s = N;
     auto addr = [&](int pos) -> int {
         if (axis == 0) return padded<N>(pos, lo, hi);
         if (axis == 1) return padded<N>(lo, pos, hi);
@@ -390,6 +392,7 @@ __global__ void velocity1d_kernel(VelocityArgs a) {
     double cc = a.qm * a.eb[c * 6] * a.dt / a.dv[0];
     bool fwd = cc >= 0.0;
     double ca = fwd ? cc : -cc;
+    if (!(ca < (double)n)) ca = (double)n;
     int s = (int)floor(ca);
     T alpha = (T)(ca - s);
     const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);

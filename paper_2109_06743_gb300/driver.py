@@ -121,7 +121,7 @@ class Simulation:
                 mark("fit_solve")
                 abi.moment_fit_solve(ctx, k, self.mom_t1[k], use_mlp, None, None, s)
                 mark("fit_exchange")
-                abi.moment_fit_exchange(ctx, k, self.mom_t1[k], None, None, self.mom_t[k], s)
+                abi.moment_fit_exchange(ctx, k, self.mom_t1[k], self.mom_t[k], s)
         else:
             self.mom_t, self.mom_t1 = self.mom_t1, self.mom_t
         mark("maxwell")
