@@ -167,6 +167,9 @@ struct WarpScratch {
     double tgt[10];    // targets of the current fit
     double coef[16];   // result of the current fit
     double wc[3], h[3], u0[3], sg[3];
+    float shift[3];    // moment weights use c - shift (origin near the mass)
+    double Jd[100];    // FP64 Gram matrix of the precise mode
+    double dd[10];     // FP64 Newton step of the precise mode
 };
 
 // Index-space coefficients of the exponent, with centred indices
@@ -297,6 +300,7 @@ __device__ void eval_fast(WarpScratch& ws, bool want_gram) {
     constexpr int R = (N * N + 31) / 32;
     const int l0 = lane * R;
     const int l1 = min(N * N, l0 + R);
+    const float shx = ws.shift[0], shy = ws.shift[1], shz = ws.shift[2];
     {
         const df rho_in = df_of(e_in), rho_j = df_of(e_j), exy = df_of(e_xy);
         acc m[10];
@@ -318,14 +322,14 @@ __device__ void eval_fast(WarpScratch& ws, bool want_gram) {
             df M = Ms, r = rs;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                const float ci = (float)i - hN;
+                const float ci = ((float)i - hN) - shx;
                 acc_add(S0, M.hi, M.lo);
                 acc_addc(S1, M.hi, M.lo, ci);
                 acc_addc(S2, M.hi, M.lo, ci * ci);
                 M = df_mul(M, r);
                 r = df_mul(r, rho_in);
             }
-            line_to_cell(m, S0, S1, S2, cj, ck);
+            line_to_cell(m, S0, S1, S2, cj - shy, ck - shz);
             Ms = df_mul(Ms, rl);
             rl = df_mul(rl, rho_j);
             rs = df_mul(rs, exy);
@@ -362,7 +366,7 @@ __device__ void eval_fast(WarpScratch& ws, bool want_gram) {
             float M = ms, r = r0;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                const float ci = (float)i - hN, c2 = ci * ci;
+                const float ci = ((float)i - hN) - shx, c2 = ci * ci;
                 T[0] += M;
                 T[1] = fmaf(M, ci, T[1]);
                 T[2] = fmaf(M, c2, T[2]);
@@ -371,7 +375,7 @@ __device__ void eval_fast(WarpScratch& ws, bool want_gram) {
                 M *= r;
                 r *= rin;
             }
-            gram_line(g, T, cj, ck);
+            gram_line(g, T, cj - shy, ck - shz);
             ms *= rls;
             rls *= rj;
             r0 *= rxy;
@@ -405,10 +409,12 @@ __device__ void eval_slow(WarpScratch& ws, bool want_gram) {
         const double C = kc[0] + kc[2] * cj + kc[3] * ck + kc[7] * cj * cj + kc[8] * cj * ck + kc[9] * ck * ck;
         double S0 = 0, S1 = 0, S2 = 0;
         float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        const double shx = ws.shift[0];
 #pragma unroll 1
         for (int i = 0; i < N; ++i) {
-            const double ci = i - hN;
-            const double M = exp(C + ci * (B + kc[4] * ci));
+            const double cq = i - hN;
+            const double M = exp(C + cq * (B + kc[4] * cq));
+            const double ci = cq - shx;
             S0 += M;
             S1 = fma(M, ci, S1);
             S2 = fma(M, ci * ci, S2);
@@ -421,9 +427,10 @@ __device__ void eval_slow(WarpScratch& ws, bool want_gram) {
                 T[4] = fmaf(Mf, cf * cf * cf * cf, T[4]);
             }
         }
-        m[0] += S0; m[1] += S1; m[2] += cj * S0; m[3] += ck * S0; m[4] += S2;
-        m[5] += cj * S1; m[6] += ck * S1; m[7] += cj * cj * S0; m[8] += cj * ck * S0; m[9] += ck * ck * S0;
-        if (want_gram) gram_line(g, T, (float)cj, (float)ck);
+        const double sj = cj - ws.shift[1], sk = ck - ws.shift[2];
+        m[0] += S0; m[1] += S1; m[2] += sj * S0; m[3] += sk * S0; m[4] += S2;
+        m[5] += sj * S1; m[6] += sk * S1; m[7] += sj * sj * S0; m[8] += sj * sk * S0; m[9] += sk * sk * S0;
+        if (want_gram) gram_line(g, T, (float)sj, (float)sk);
     }
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
@@ -545,6 +552,92 @@ __device__ bool solve10f(WarpScratch& ws) {
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// Precise mode (cells where the FP32 Jacobian does not converge within a
+// few iterations, e.g. Maxwellians truncated by the velocity box): the Gram
+// matrix in FP64 with one exponential per cell, solved in FP64 by lane 0.
+template <int N>
+__device__ bool precise_step(WarpScratch& ws, const double* wc, const double* h, double vol, double Gl) {
+    const int lane = threadIdx.x & 31;
+    constexpr double hN = 0.5 * (N - 1);
+    const double* kc = ws.kc;
+    double W[35];
+#pragma unroll
+    for (int q = 0; q < 35; ++q) W[q] = 0.0;
+#pragma unroll 1
+    for (int l = lane; l < N * N; l += 32) {
+        const int j = l % N, k = l / N;
+        const double cj = j - hN, ck = k - hN;
+        const double B = kc[1] + kc[5] * cj + kc[6] * ck;
+        const double C = kc[0] + kc[2] * cj + kc[3] * ck + kc[7] * cj * cj + kc[8] * cj * ck + kc[9] * ck * ck;
+        double T[5] = {0, 0, 0, 0, 0};
+#pragma unroll 1
+        for (int i = 0; i < N; ++i) {
+            const double ci = i - hN;
+            const double M = exp(C + ci * (B + kc[4] * ci));
+            const double w = wc[0] + h[0] * ci;
+            double p = M;
+            for (int q = 0; q < 5; ++q) {
+                T[q] += p;
+                p *= w;
+            }
+        }
+        const double wy = wc[1] + h[1] * cj, wz = wc[2] + h[2] * ck;
+        double py[5], pz[5];
+        py[0] = pz[0] = 1.0;
+        for (int q = 1; q < 5; ++q) {
+            py[q] = py[q - 1] * wy;
+            pz[q] = pz[q - 1] * wz;
+        }
+        for (int a = 0; a <= 4; ++a)
+            for (int b = 0; b <= 4 - a; ++b)
+                for (int c = 0; c <= 4 - a - b; ++c) W[mono4(a, b, c)] += T[a] * py[b] * pz[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 35; ++q) W[q] = warp_sum(W[q]) * vol;
+    const int E[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                          {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+    double rhs = -Gl;
+    double g[10];
+    for (int q = 0; q < 10; ++q) g[q] = bcast(rhs, q);
+    int ok = 1;
+    if (lane == 0) {
+        double* J = ws.Jd;
+        for (int e = 0; e < 100; ++e) {
+            int a = e / 10, b = e % 10;
+            J[e] = W[mono4(E[a][0] + E[b][0], E[a][1] + E[b][1], E[a][2] + E[b][2])];
+        }
+        for (int i = 0; i < 10 && ok; ++i)
+            for (int j = 0; j <= i; ++j) {
+                double s = J[i * 10 + j];
+                for (int k = 0; k < j; ++k) s -= J[i * 10 + k] * J[j * 10 + k];
+                if (i == j) {
+                    if (!(s > 0.0)) {
+                        ok = 0;
+                        break;
+                    }
+                    J[i * 10 + i] = sqrt(s);
+                } else {
+                    J[i * 10 + j] = s / J[j * 10 + j];
+                }
+            }
+        if (ok) {
+            double y[10];
+            for (int i = 0; i < 10; ++i) {
+                double s = g[i];
+                for (int k = 0; k < i; ++k) s -= J[i * 10 + k] * y[k];
+                y[i] = s / J[i * 10 + i];
+            }
+            for (int i = 9; i >= 0; --i) {
+                double s = y[i];
+                for (int k = i + 1; k < 10; ++k) s -= J[k * 10 + i] * ws.dd[k];
+                ws.dd[i] = s / J[i * 10 + i];
+            }
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 template <int N>
 __device__ __forceinline__ void evaluate(WarpScratch& ws, const double* eta, const double* wc, const double* h,
                                          bool gram) {
@@ -581,9 +674,16 @@ __device__ int fit_one(WarpScratch& ws, const FitArgs& a, int* iters) {
             ws.sg[q] = (double)sqrtf(Th[q * 4]);
             ws.h[q] = a.dv[q] / ws.sg[q];
             ws.wc[q] = (a.vmin[q] + 0.5 * N * a.dv[q] - ws.u0[q]) / ws.sg[q];
+            // integer cell nearest to the mean: origin of the moment weights
+            float ic = rintf((float)((ws.u0[q] - a.vmin[q]) / a.dv[q] - 0.5));
+            ic = fminf(fmaxf(ic, 0.f), (float)(N - 1));
+            ws.shift[q] = ic - 0.5f * (N - 1);
         }
         __syncwarp();
     }
+    // w at the origin of the moment weights
+    double wm[3];
+    for (int q = 0; q < 3; ++q) wm[q] = ws.wc[q] + ws.h[q] * (double)ws.shift[q];
     const double vol = a.dv[0] * a.dv[1] * a.dv[2];
     // targets in w-space, lane t < 10 holds T_t
     double Tl = 0.0;
@@ -634,7 +734,7 @@ __device__ int fit_one(WarpScratch& ws, const FitArgs& a, int* iters) {
     evaluate<N>(ws, ws.eta, ws.wc, ws.h, true);
     bool have_gram = true;
     for (it = 0; it <= a.max_iter; ++it) {
-        const double Dl = lane < 10 ? w_moment(lane, ws.m, ws.wc, ws.h, vol) : 0.0;
+        const double Dl = lane < 10 ? w_moment(lane, ws.m, wm, ws.h, vol) : 0.0;
         const double Gl = Dl - Tl;
         if (!__all_sync(0xffffffffu, isfinite(Gl))) break;
         if (__all_sync(0xffffffffu, fabs(Gl) <= a.tol * n)) {
@@ -646,25 +746,36 @@ __device__ int fit_one(WarpScratch& ws, const FitArgs& a, int* iters) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
         gmax = bcastf(gmax, 0);
-        if (!have_gram) {
-            evaluate<N>(ws, ws.eta, ws.wc, ws.h, true);  // refresh the Jacobian at this point
-            have_gram = true;
+        const bool precise = it >= 6;
+        if (precise) {
+            // FP64 Jacobian at this point (kc of the current parameters)
+            index_coefficients(ws.eta, ws.wc, ws.h, ws.kc);
+            if (!precise_step<N>(ws, ws.wc, ws.h, vol, Gl)) break;
+            if (lane < 10) ws.dl[lane] = (float)0.0;
+            __syncwarp();
+        } else {
+            if (!have_gram) {
+                evaluate<N>(ws, ws.eta, ws.wc, ws.h, true);  // refresh the Jacobian at this point
+                have_gram = true;
+            }
+            gram_matrix(ws, wm, ws.h, (float)vol);
+            if (lane < 10) ws.rhs[lane] = -(float)Gl;
+            __syncwarp();
+            if (!solve10f(ws)) break;
+            if (lane < 10) ws.dd[lane] = (double)ws.dl[lane];
+            __syncwarp();
         }
-        gram_matrix(ws, ws.wc, ws.h, (float)vol);
-        if (lane < 10) ws.rhs[lane] = -(float)Gl;
-        __syncwarp();
-        if (!solve10f(ws)) break;
         // damped step: backtracking on L(eta) = D_0 - eta . T while far away
         const bool damp = gmax > 1e-6f;
         double L0 = 0.0, gd = 0.0;
         if (damp) {
             L0 = bcast(Dl, 0) - warp_sum(lane < 10 ? ws.eta[lane] * Tl : 0.0);
-            gd = warp_sum(lane < 10 ? Gl * (double)ws.dl[lane] : 0.0);
+            gd = warp_sum(lane < 10 ? Gl * ws.dd[lane] : 0.0);
         }
         double lamb = 1.0;
         const bool gram_next = gmax > 1e-7f;
         for (int ls = 0; ls < 40; ++ls) {
-            if (lane < 10) ws.et[lane] = ws.eta[lane] + lamb * (double)ws.dl[lane];
+            if (lane < 10) ws.et[lane] = ws.eta[lane] + lamb * ws.dd[lane];
             __syncwarp();
             evaluate<N>(ws, ws.et, ws.wc, ws.h, gram_next);
             if (!damp) break;
