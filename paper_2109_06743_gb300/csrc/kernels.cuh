@@ -72,6 +72,7 @@ struct FitArgs {
     int max_iter;
 };
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
+cudaError_t launch_newton3d(const FitArgs& a, cudaStream_t st);
 cudaError_t launch_theta(const double* coef, const int* status, int which, double* theta, long long ncell, int nvdim,
                          cudaStream_t st);
 
