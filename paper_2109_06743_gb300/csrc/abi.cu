@@ -53,14 +53,14 @@ long long vblock_of(const vl_desc& d, int s) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t shears, coef_v, coef_f, status, u1, u2, cur, counters, total;
+    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, counters, total;
 };
 
 Layout layout_of(const vl_desc& d) {
     Layout L;
     const size_t nc = (size_t)ncell_of(d);
     size_t off = 0;
-    L.shears = off; off = align256(off + nc * 20 * sizeof(double));
+    L.cellwork = off; off = align256(off + nc * 20 * sizeof(double));
     L.coef_v = off; off = align256(off + nc * 16 * sizeof(double));
     L.coef_f = off; off = align256(off + nc * 16 * sizeof(double));
     L.status = off; off = align256(off + nc * 2 * sizeof(int));
@@ -163,7 +163,7 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     c->yee = yee_dev;
     c->eb = eb_dev;
     char* w = static_cast<char*>(work_dev);
-    c->ws.shears = reinterpret_cast<double*>(w + L.shears);
+    c->ws.cellwork = reinterpret_cast<double*>(w + L.cellwork);
     c->ws.coef_v = reinterpret_cast<double*>(w + L.coef_v);
     c->ws.coef_f = reinterpret_cast<double*>(w + L.coef_f);
     c->ws.fit_status = reinterpret_cast<int*>(w + L.status);
@@ -248,10 +248,18 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
     } else {
         a.mode = 0;
         a.ncol = 32;
-        while (a.ncol > 8 && (size_t)a.n * a.ncol * es > 96 * 1024) a.ncol /= 2;
+        while (a.ncol > 8 && (size_t)a.n * a.ncol * es > 64 * 1024) a.ncol /= 2;
         a.nchunks = (int)((V + a.ncol - 1) / a.ncol);
     }
-    if ((size_t)a.n * a.ncol * es > 200 * 1024 || a.ncol > 256)
+    // cp.async staging needs every column run (V, nvx and the tile width in
+    // bytes) to be a multiple of 16 bytes; the base of f is 256-byte aligned
+    {
+        const long long run = wall ? a.nvx : V;
+        a.vec = (run * es) % 16 == 0 && ((long long)a.ncol * es) % 16 == 0 && (V * es) % 16 == 0;
+    }
+    const size_t tile_bytes = (size_t)a.n * a.ncol * es;
+    a.nbuf = 2 * tile_bytes <= 200 * 1024 ? 2 : 1;
+    if (tile_bytes > 200 * 1024 || a.ncol > 256)
         return fail(ctx, VL_ENOTSUP, "spatial line too long for one shared-memory tile (%d cells)", a.n);
     return cuda_check(ctx, vl::launch_pfc_space(a, d.precision, (cudaStream_t)stream), "pfc_advect_x");
 }
@@ -264,7 +272,7 @@ vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream
     vl::VelocityArgs a;
     a.f = ctx->f[s];
     a.eb = ctx->eb;
-    a.shears = ctx->ws.shears;
+    a.shears = ctx->ws.cellwork;
     a.mom_out = mom_out;
     a.ncell = ncell_of(d);
     a.nv = d.nv[s][0];
@@ -340,6 +348,7 @@ vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, double* mo
     x.nv = d.nv[s][0];
     fill_box(d, s, x.vmin, x.dv);
     x.conv = ctx->conv[s];
+    x.par = ctx->ws.cellwork;
     return cuda_check(ctx, vl::launch_exchange(x, d.nvdim, d.precision, (cudaStream_t)stream),
                       "moment_fit (exchange)");
 }

@@ -30,7 +30,9 @@ void count_launch(int n = 1);
 
 // Workspace layout offsets (bytes) computed by the ABI layer.
 struct Workspace {
-    double* shears;       // [ncell][5][4] shear factors of the velocity map
+    double* cellwork;     // [ncell][20] per-cell scratch: the shear factors of the velocity
+                          // map (pfc_advect_v), then the Maxwellian line parameters of
+                          // the exchange (moment_fit_exchange)
     double* coef_v;       // [ncell][16] fit coefficients of f_M,V
     double* coef_f;       // [ncell][16] fit coefficients of f_M,F
     int* fit_status;      // [ncell][2] status of the V and F fits

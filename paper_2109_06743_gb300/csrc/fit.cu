@@ -3,11 +3,12 @@
 // conversion of fit coefficients to the paper's parameters. The 2D3V Newton
 // fits are in newton.cu.
 //
-// exchange_kernel: one CTA per cell: f <- f - f_M,V + f_M,F, clip negative
-// values and rescale the cell to n_V (limiter of Algorithm 1), fused with the
-// moments of the new f.
+// exchange_kernel: f <- f - f_M,V + f_M,F, clip negative values and rescale
+// the cell to n_V (limiter of Algorithm 1), fused with the moments of the
+// new f; the Maxwellians' line parameters come from exchange_params_kernel.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "block_moments.cuh"
 
 namespace vl {
 
@@ -87,109 +88,179 @@ __global__ void coef_to_theta_kernel(const double* coef, const int* status, int 
 
 // ------------------------------------------------------------------ exchange
 
-// index-space parameters of one Maxwellian for the exchange: the exponent
-// at cell (i, j, k) is lognorm - 1/2 d^T Pt d with d = (i, j, k) - ic (ic =
-// index of the peak); computed from the fit coefficients (eta, u0, sigma):
-// q(w) = eta0 + lambda.w + w^T mu w has its peak at w* = -mu^-1 lambda / 2
-// with value eta0 + lambda.w*/2, and w = w0 + h * index with h = dv/sigma.
-struct MaxwIdx {
-    double ic[3];
-    double Pt[6];  // xx xy xz yy yz zz
-    double lognorm;
-    int valid;
-};
+// Line parameters of one fitted Maxwellian for the exchange, from the fit
+// coefficients (eta, u0, sigma): q(w) = eta0 + lambda.w + w^T mu w has its
+// peak at w* = -mu^-1 lambda / 2 with value L = eta0 + lambda.w*/2, and
+// w = w0 + h * index with h = dv/sigma, so in index space the exponent is
+// L - 1/2 d^T P d with d = index - ic, ic = (w* - w0)/h, P = -2 H mu H.
+// Along a v_z line (i, j fixed) this is
+//   E(k) = Ec - hz (k - kc)^2,
+//   Ec = L - 1/2 (Sxx dx^2 + 2 Sxy dx dy + Syy dy^2),  kc = icz + gx dx + gy dy,
+// with (dx, dy) = (i, j) - (icx, icy), hz = Pzz/2, S = P_tt - p p^T / Pzz the
+// Schur complement (p = (Pxz, Pyz)) and g = -p / Pzz.
+// par[10] = (icx, icy, icz, Sxx, Sxy, Syy, gx, gy, hz, L); hz = 0 marks a fit
+// that is not used.
+constexpr int kPar = 10;
 
-__device__ void maxwellian_index_params(const double* k, int valid, const double* vmin, const double* dv,
-                                        MaxwIdx* o) {
-    o->valid = valid;
+__device__ void maxwellian_line_params(const double* k, bool valid, const double* vmin, const double* dv, double* par) {
+    for (int q = 0; q < kPar; ++q) par[q] = 0.0;
     if (!valid) return;
     double mu[9] = {k[4], 0.5 * k[5], 0.5 * k[6], 0.5 * k[5], k[7], 0.5 * k[8], 0.5 * k[6], 0.5 * k[8], k[9]};
     double mi[9];
     inv3(mu, mi);
     const double lam[3] = {k[1], k[2], k[3]};
-    double ws[3], q = k[0];
+    double ws[3], L = k[0], h[3], ic[3];
     for (int a = 0; a < 3; ++a) {
         ws[a] = -0.5 * (mi[a * 3] * lam[0] + mi[a * 3 + 1] * lam[1] + mi[a * 3 + 2] * lam[2]);
-        q += 0.5 * lam[a] * ws[a];
+        L += 0.5 * lam[a] * ws[a];
     }
     const double* u0 = k + 10;
     const double* sg = k + 13;
-    double h[3];
     for (int a = 0; a < 3; ++a) {
         h[a] = dv[a] / sg[a];
-        double w0 = (vmin[a] + 0.5 * dv[a] - u0[a]) / sg[a];
-        o->ic[a] = (ws[a] - w0) / h[a];
+        const double w0 = (vmin[a] + 0.5 * dv[a] - u0[a]) / sg[a];
+        ic[a] = (ws[a] - w0) / h[a];
     }
-    o->Pt[0] = -2.0 * h[0] * h[0] * mu[0];
-    o->Pt[1] = -2.0 * h[0] * h[1] * mu[1];
-    o->Pt[2] = -2.0 * h[0] * h[2] * mu[2];
-    o->Pt[3] = -2.0 * h[1] * h[1] * mu[4];
-    o->Pt[4] = -2.0 * h[1] * h[2] * mu[5];
-    o->Pt[5] = -2.0 * h[2] * h[2] * mu[8];
-    o->lognorm = q;
+    double P[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) P[a * 3 + b] = -2.0 * h[a] * h[b] * mu[a * 3 + b];
+    const double pzz = P[8];
+    if (!(pzz > 0.0) || !isfinite(L)) return;
+    const double gx = -P[2] / pzz, gy = -P[5] / pzz;
+    par[0] = ic[0];
+    par[1] = ic[1];
+    par[2] = ic[2];
+    par[3] = P[0] + P[2] * gx;
+    par[4] = P[1] + P[2] * gy;
+    par[5] = P[4] + P[5] * gy;
+    par[6] = gx;
+    par[7] = gy;
+    par[8] = 0.5 * pzz;
+    par[9] = L;
 }
 
-// Maxwellian along the x line (j, k): values M_i for i = 0..N-1 by recurrence.
-template <typename T, int N>
-__device__ __forceinline__ void maxwellian_line(const MaxwIdx& p, int j, int k, T (&out)[N]) {
-    if (!p.valid) {
+__global__ void exchange_params_kernel(ExchangeArgs a) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= 2 * a.ncell) return;
+    const long long cell = g >> 1;
+    const int w = (int)(g & 1);
+    const int stv = a.status[cell * 2], stf = a.status[cell * 2 + 1];
+    const bool valid = stv != 2 && stf != 2;
+    maxwellian_line_params((w == 0 ? a.coef_v : a.coef_f) + cell * kCoef, valid, a.vmin, a.dv,
+                           a.par + cell * 2 * kPar + w * kPar);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// r[k] += sgn * M(i, j, k) along the v_z line of this thread.
+// FP32: per element, exponent in base 2 and ex2.approx (relative error
+// about 2^-22).
+template <int N>
+__device__ __forceinline__ void add_maxwellian(float (&r)[N], const double* pd, int i, int j, float sgn,
+                                               const double*) {
+    const float hz = (float)pd[8];
+    if (!(hz > 0.f)) return;
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float dx = (float)i - (float)pd[0], dy = (float)j - (float)pd[1];
+    const float Q = (float)pd[3] * dx * dx + 2.f * (float)pd[4] * dx * dy + (float)pd[5] * dy * dy;
+    const float kc = (float)pd[2] + (float)pd[6] * dx + (float)pd[7] * dy;
+    const float Ec2 = ((float)pd[9] - 0.5f * Q) * kLog2e;
+    const float hz2 = hz * kLog2e;
 #pragma unroll
-        for (int i = 0; i < N; ++i) out[i] = T(0);
+    for (int k = 0; k < N; ++k) {
+        const float tk = (float)k - kc;
+        r[k] = fmaf(sgn, ex2_approx(fmaf(-hz2, tk * tk, Ec2)), r[k]);
+    }
+}
+
+// FP64: M(k) = C A^m G(m) with k0 = floor(kc) (clamped to the line),
+// m = k - k0, delta = kc - k0, C = exp(Ec - hz delta^2), A = exp(2 hz delta)
+// and the per-cell table G(m) = exp(-hz m^2); three exponentials per line.
+// The factors stay in range for hz <= 8 (sigma above a quarter cell);
+// narrower Maxwellians take one exponential per element.
+template <int N>
+__device__ __forceinline__ void add_maxwellian(double (&r)[N], const double* pd, int i, int j, double sgn,
+                                               const double* G) {
+    const double hz = pd[8];
+    if (!(hz > 0.0)) return;
+    const double dx = i - pd[0], dy = j - pd[1];
+    const double Q = pd[3] * dx * dx + 2.0 * pd[4] * dx * dy + pd[5] * dy * dy;
+    const double kc = pd[2] + pd[6] * dx + pd[7] * dy;
+    const double Ec = pd[9] - 0.5 * Q;
+    if (hz > 8.0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const double tk = k - kc;
+            r[k] += sgn * exp(Ec - hz * tk * tk);
+        }
         return;
     }
-    const T dy = (T)(j - p.ic[1]), dz = (T)(k - p.ic[2]);
-    const T dx0 = (T)(0 - p.ic[0]);
-    const T Pxx = (T)p.Pt[0], Pxy = (T)p.Pt[1], Pxz = (T)p.Pt[2];
-    const T Pyy = (T)p.Pt[3], Pyz = (T)p.Pt[4], Pzz = (T)p.Pt[5];
-    const T b = Pxy * dy + Pxz * dz;
-    // exponent at i: -1/2 (Pxx dx^2 + 2 dx b + Pyy dy^2 + 2 Pyz dy dz + Pzz dz^2)
-    const T q0 = T(-0.5) * (Pxx * dx0 * dx0 + T(2) * dx0 * b + Pyy * dy * dy + T(2) * Pyz * dy * dz + Pzz * dz * dz);
-    T M = exp(q0 + (T)p.lognorm);
-    T r = exp(T(-0.5) * Pxx * (T(2) * dx0 + T(1)) - b);
-    const T rho = exp(-Pxx);
+    double k0 = floor(kc);
+    k0 = fmin(fmax(k0, 0.0), (double)(N - 1));
+    const double delta = kc - k0;
+    const double C = sgn * exp(Ec - hz * delta * delta);
+    const double A = exp(2.0 * hz * delta);
+    double Ap = exp(-2.0 * hz * delta * k0);
+    const double* Gk = G + (N - 1) - (int)k0;  // Gk[k] = G(k - k0)
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        out[i] = M;
-        M *= r;
-        r *= rho;
+    for (int k = 0; k < N; ++k) {
+        r[k] += C * (Ap * Gk[k]);
+        Ap *= A;
     }
 }
 
+constexpr int ex_threads(int n) { return ((n * n + 31) / 32) * 32; }
+
+// One CTA per cell at a time (persistent): thread t < N^2 owns the v_z line
+// (i, j) = (t mod N, t / N), so each load and store of the block is a
+// contiguous run of N^2 values. f <- f - M_V + M_F; if any value is negative
+// all are clipped at zero and the cell rescaled to n_V (the limiter of
+// Algorithm 1); cells whose fits are invalid are left alone. Fused with the
+// moments of the new f.
 template <typename T, int N>
-__global__ void exchange_kernel(ExchangeArgs a) {
-    __shared__ MaxwIdx mp[2];
+__global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a) {
     __shared__ double red[20 * 32 + 20];
     __shared__ double ssum[32];
     __shared__ int sneg[32];
+    __shared__ double spar[2 * kPar];
+    __shared__ double gtab[2][sizeof(T) == 8 ? 2 * N - 1 : 1];
     T* f = reinterpret_cast<T*>(a.f);
     constexpr long long V = (long long)N * N * N;
+    constexpr int NN = N * N;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
+    const bool active = t < NN;
+    const int i = active ? t % N : 0, j = active ? t / N : 0;
     const double vol = a.dv[0] * a.dv[1] * a.dv[2];
     for (long long cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
+        T r[N];
+        const T* src = f + cell * V + t;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) r[k] = src[(long long)k * NN];
+        }
         const int stv = a.status[cell * 2], stf = a.status[cell * 2 + 1];
         const bool skip = (stv == 2 || stf == 2);
-        if (t < 2) maxwellian_index_params((t == 0 ? a.coef_v : a.coef_f) + cell * kCoef, (t == 0 ? stv : stf) != 2, a.vmin, a.dv, &mp[t]);
+        if (t < 2 * kPar) spar[t] = a.par[cell * 2 * kPar + t];
+        if (sizeof(T) == 8 && t < 2 * (2 * N - 1)) {
+            const int w = t / (2 * N - 1), m = t % (2 * N - 1) - (N - 1);
+            const double hz = a.par[cell * 2 * kPar + w * kPar + 8];
+            gtab[w][sizeof(T) == 8 ? t % (2 * N - 1) : 0] = exp(-hz * (double)(m * m));
+        }
         __syncthreads();
-        T r[N];
-        const int j = t % N, k = t / N;
-        const bool active = t < N * N;
         T lsum = T(0);
         int neg = 0;
-        if (active) {
-            const T* src = f + cell * V + (long long)(k * N + j) * N;
+        if (active && !skip) {
+            add_maxwellian<N>(r, spar, i, j, T(-1), gtab[0]);
+            add_maxwellian<N>(r, spar + kPar, i, j, T(1), gtab[1]);
 #pragma unroll
-            for (int i = 0; i < N; ++i) r[i] = src[i];
-            if (!skip) {
-                T mv[N], mf[N];
-                maxwellian_line<T, N>(mp[0], j, k, mv);
-                maxwellian_line<T, N>(mp[1], j, k, mf);
-#pragma unroll
-                for (int i = 0; i < N; ++i) {
-                    r[i] = r[i] - mv[i] + mf[i];
-                    neg |= r[i] < T(0);
-                    lsum += fmax(r[i], T(0));
-                }
+            for (int k = 0; k < N; ++k) {
+                neg |= r[k] < T(0);
+                lsum += fmax(r[k], T(0));
             }
         }
         // block reduction: any negative, sum of the clipped values
@@ -216,54 +287,23 @@ __global__ void exchange_kernel(ExchangeArgs a) {
 #pragma unroll
         for (int q = 0; q < 20; ++q) m[q] = T(0);
         if (active) {
-            T* dst = f + cell * V + (long long)(k * N + j) * N;
+            T* dst = f + cell * V + t;
             const T c = T(0.5) * T(N - 1);
             T S0 = 0, S1 = 0, S2 = 0, S3 = 0;
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                T v = anyneg ? fmax(r[i], T(0)) * scale : r[i];
-                dst[i] = v;
-                T xi = T(i) - c;
-                T v1 = v * xi, v2 = v1 * xi;
+            for (int k = 0; k < N; ++k) {
+                const T v = anyneg ? fmax(r[k], T(0)) * scale : r[k];
+                if (!skip) dst[(long long)k * NN] = v;
+                const T z = T(k) - c;
+                const T v1 = v * z, v2 = v1 * z;
                 S0 += v;
                 S1 += v1;
                 S2 += v2;
-                S3 += v2 * xi;
+                S3 += v2 * z;
             }
-            if (a.mom_out) {
-                const T e = T(j) - c, z = T(k) - c;
-                const T e2 = e * e, z2 = z * z, ez = e * z;
-                m[0] = S0; m[1] = S1; m[2] = e * S0; m[3] = z * S0;
-                m[4] = S2; m[5] = e * S1; m[6] = z * S1; m[7] = e2 * S0; m[8] = ez * S0; m[9] = z2 * S0;
-                m[10] = S3; m[11] = e * S2; m[12] = z * S2; m[13] = e2 * S1; m[14] = ez * S1; m[15] = z2 * S1;
-                m[16] = e2 * e * S0; m[17] = e2 * z * S0; m[18] = e * z2 * S0; m[19] = z2 * z * S0;
-            }
+            if (a.mom_out) line_products_z<T, N>(m, S0, S1, S2, S3, i, j);
         }
-        if (a.mom_out) {
-#pragma unroll
-            for (int q = 0; q < 20; ++q) {
-                T v = m[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                m[q] = v;
-            }
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < 20; ++q) red[warp * 20 + q] = (double)m[q];
-            __syncthreads();
-            double* im = red + 20 * 32;
-            if (t < 20) {
-                double acc = 0.0;
-                for (int w = 0; w < nwarp; ++w) acc += red[w * 20 + t];
-                im[t] = acc;
-            }
-            __syncwarp();
-            if (t < 20) {
-                double acc = 0.0;
-                for (int q = 0; q < a.conv.nterm[t]; ++q) acc += a.conv.coef[t][q] * im[a.conv.idx[t][q]];
-                a.mom_out[cell * 20 + t] = acc;
-            }
-        }
+        if (a.mom_out) reduce_moments<T>(m, red, a.mom_out + cell * 20, a.conv);
         __syncthreads();
     }
 }
@@ -452,7 +492,14 @@ cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st) {
 
 template <typename T, int N>
 static cudaError_t launch_exchange_n(const ExchangeArgs& a, cudaStream_t st) {
-    const int threads = ((N * N + 31) / 32) * 32;
+    {
+        const long long n = 2 * a.ncell;
+        exchange_params_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int threads = ex_threads(N);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exchange_kernel<T, N>, threads, 0);
     if (per_sm < 1) per_sm = 1;

@@ -10,12 +10,14 @@ struct SpaceSweepArgs {
     void* f;
     int n;                  // cells along the sweep axis
     long long row_stride;   // elements between neighbouring cells along the line
-    long long line_stride;  // elements between neighbouring lines (blockIdx.y)
+    long long line_stride;  // elements between neighbouring lines
     int nlines;             // number of lines
     long long V;            // velocity block size
     int wall;               // reflecting walls (mirror rows use the v_y-mirrored column)
     int ncol, nchunks;      // velocity columns per tile, tiles per line
     int mode;               // 0: contiguous columns, 1: v_y mirror pairs
+    int vec;                // column runs 16-byte aligned: stage tiles with cp.async
+    int nbuf;               // tile buffers in shared memory (2: prefetch the next tile)
     int nvx, nvy;
     int axis_div, axis_mod; // velocity index of the sweep axis: (vi / div) % mod
     double vmin_a, dv_a, dt_over_h;
@@ -40,6 +42,7 @@ struct VelocityArgs {
     long long ncell;
     int nv;                 // cubic block edge (2D3V); 1D1V: line length
     int nshear;
+    int nbuf;               // block buffers in shared memory (set by the launcher)
     double qm, dt;
     double vmin[3], dv[3];
     MomConv conv;
@@ -84,6 +87,7 @@ struct ExchangeArgs {
     const int* status;
     double* mom_out;        // moments of the new f or null
     unsigned long long* counters;
+    double* par;            // [ncell][2][10] scratch: Maxwellian line parameters
     long long ncell;
     int nv;
     double vmin[3], dv[3];

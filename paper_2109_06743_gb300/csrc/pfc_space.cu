@@ -1,13 +1,15 @@
 // Spatial PFC sweeps (paper Sec. 2.1: PFC scheme of Filbet, Sonnendruecker
 // and Bertrand 2001; Sec. 3.3: reflecting walls in y).
 //
-// One CTA owns one spatial line (a y row for the x sweep, an x column for the
-// y sweep) for a tile of velocity columns. The whole line of the tile is
-// staged in shared memory (rows along the sweep axis, columns = velocity
-// indices, so every global access is a contiguous run of the velocity block),
-// then each thread walks a segment of one column with a sliding window and
-// writes the result straight back to global memory. Since a CTA reads
-// everything it writes before writing, the sweep is in place.
+// A tile is one spatial line (a y row for the x sweep, an x column for the y
+// sweep) times W velocity columns: rows along the sweep axis, each row a
+// contiguous run of the velocity block, so every global access is a
+// 64-128 byte segment. Persistent CTAs walk the tiles; each tile is staged in
+// shared memory with 16-byte cp.async copies, double buffered, so the copy of
+// tile t+1 is in flight while tile t is computed. Each thread walks a segment
+// of one column with a sliding window and writes the result straight back to
+// global memory; a CTA reads its whole tile before writing it, so the sweep
+// is in place.
 //
 // For a displacement c = v dt / dx = s + alpha (alpha in [0,1)) the PFC update
 // is f_i <- g_{i-s}, g_j = f_j - phi_j + phi_{j-1}, with the limited flux
@@ -28,114 +30,178 @@ __device__ __forceinline__ T pfc_phi(T alpha, T A, T B, T fm, T f0, T fp) {
     return alpha * (f0 + A * up + B * dn);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) pfc_space_kernel(SpaceSweepArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
-    T* f = reinterpret_cast<T*>(a.f);
-    const int ncol = a.ncol;
-    const int n = a.n;
-    const long long base = (long long)blockIdx.y * a.line_stride;
-    const int chunk = blockIdx.x;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
-    // column -> velocity index (and its v_y mirror within the tile)
-    auto col_vi = [&](int col, long long* vi, int* mcol) -> bool {
-        if (a.mode == 0) {
-            long long v = (long long)chunk * ncol + col;
-            *vi = v;
-            *mcol = col;
-            return v < a.V;
-        }
-        int half = (a.nvy + 1) / 2;
-        int k = chunk / half, j = chunk % half;
-        int jm = a.nvy - 1 - j;
-        if (col < a.nvx) {
-            *vi = ((long long)k * a.nvy + j) * a.nvx + col;
-            *mcol = (jm == j) ? col : col + a.nvx;
-            return true;
-        }
-        if (jm == j || col >= 2 * a.nvx) return false;
-        *vi = ((long long)k * a.nvy + jm) * a.nvx + (col - a.nvx);
-        *mcol = col - a.nvx;
-        return true;
-    };
-
-    // stage the tile: rows along the line, contiguous velocity columns
-    for (int idx = threadIdx.x; idx < n * ncol; idx += blockDim.x) {
-        int r = idx / ncol, col = idx - r * ncol;
-        long long vi;
-        int mc;
-        if (col_vi(col, &vi, &mc)) tile[idx] = f[base + (long long)r * a.row_stride + vi];
+// velocity index of tile column col, and the column holding its v_y mirror
+__device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int col, long long* vi, int* mcol) {
+    if (a.mode == 0) {
+        long long v = (long long)chunk * a.ncol + col;
+        *vi = v;
+        *mcol = col;
+        return v < a.V;
     }
-    __syncthreads();
+    const int half = (a.nvy + 1) / 2;
+    const int k = chunk / half, j = chunk % half;
+    const int jm = a.nvy - 1 - j;
+    if (col < a.nvx) {
+        *vi = ((long long)k * a.nvy + j) * a.nvx + col;
+        *mcol = (jm == j) ? col : col + a.nvx;
+        return true;
+    }
+    if (jm == j || col >= 2 * a.nvx) return false;
+    *vi = ((long long)k * a.nvy + jm) * a.nvx + (col - a.nvx);
+    *mcol = col - a.nvx;
+    return true;
+}
 
-    const int nseg = blockDim.x / ncol;
-    const int col = threadIdx.x % ncol;
-    const int seg = threadIdx.x / ncol;
-    if (seg >= nseg) return;
+// issue the copies of one tile: 16-byte cp.async chunks when every column
+// run starts on a 16-byte boundary and spans a multiple of 16 bytes (a.vec),
+// else plain element loads
+template <typename T>
+__device__ __forceinline__ void load_tile(const SpaceSweepArgs& a, const T* f, T* tile, long long tidx) {
+    const int chunk = (int)(tidx % a.nchunks);
+    const long long base = (tidx / a.nchunks) * a.line_stride;
     long long vi;
-    int mcol;
-    if (!col_vi(col, &vi, &mcol)) return;
-
-    // displacement of this column in cells
-    int ia = (int)((vi / a.axis_div) % a.axis_mod);
-    double c = (a.vmin_a + (ia + 0.5) * a.dv_a) * a.dt_over_h;
-    const bool fwd = c >= 0.0;
-    double ca = fwd ? c : -c;
-    // periodic lines: a shift by whole line lengths is the identity; walls:
-    // the host guarantees ca + 3 <= n. Clamp before the int conversion.
-    if (!a.wall) ca = fmod(ca, (double)n);
-    if (!(ca <= (double)n)) ca = (double)n;
-    const int s = (int)floor(ca);
-    const T alpha = (T)(ca - s);
-    const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
-    const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
-
-    // value at reversed-frame index j (physical p = j forward, n-1-j reversed)
-    auto fetch = [&](int j) -> T {
-        int p = fwd ? j : n - 1 - j;
-        if (p >= 0 && p < n) return tile[p * ncol + col];
-        if (!a.wall) {
-            p %= n;
-            if (p < 0) p += n;
-            return tile[p * ncol + col];
+    int mc;
+    if (a.vec) {
+        constexpr int per = 16 / sizeof(T);
+        const int cpr = a.ncol / per;  // chunks per row
+        for (int idx = threadIdx.x; idx < a.n * cpr; idx += blockDim.x) {
+            const int r = idx / cpr, c = (idx - r * cpr) * per;
+            if (col_vi(a, chunk, c, &vi, &mc))
+                cp_async16(tile + r * a.ncol + c, f + base + (long long)r * a.row_stride + vi);
         }
-        p = p < 0 ? -1 - p : 2 * n - 1 - p;  // mirror row, v_y -> -v_y column
-        return tile[p * ncol + mcol];
-    };
-
-    const int L = (n + nseg - 1) / nseg;
-    const int k0 = seg * L;
-    const int k1 = min(n, k0 + L);
-    if (k0 >= k1) return;
-    int j = k0 - s;
-    T fm2 = fetch(j - 2), fm1 = fetch(j - 1), f0 = fetch(j), fp1 = fetch(j + 1);
-    T phim = pfc_phi<T>(alpha, A, B, fm2, fm1, f0);
-    for (int k = k0; k < k1; ++k) {
-        T phi = pfc_phi<T>(alpha, A, B, fm1, f0, fp1);
-        T g = f0 - phi + phim;
-        int i = fwd ? k : n - 1 - k;
-        f[base + (long long)i * a.row_stride + vi] = g;
-        ++j;
-        fm2 = fm1;
-        fm1 = f0;
-        f0 = fp1;
-        fp1 = fetch(j + 1);
-        phim = phi;
+    } else {
+        for (int idx = threadIdx.x; idx < a.n * a.ncol; idx += blockDim.x) {
+            const int r = idx / a.ncol, c = idx - r * a.ncol;
+            if (col_vi(a, chunk, c, &vi, &mc)) tile[idx] = f[base + (long long)r * a.row_stride + vi];
+        }
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) pfc_space_kernel(SpaceSweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* f = reinterpret_cast<T*>(a.f);
+    const int ncol = a.ncol, n = a.n;
+    T* const buf0 = reinterpret_cast<T*>(smem_raw);
+    T* const buf1 = buf0 + (size_t)n * ncol;
+    const long long ntiles = (long long)a.nchunks * a.nlines;
+    const int nseg = blockDim.x / ncol;
+    const int col = threadIdx.x % ncol;
+    const int seg = threadIdx.x / ncol;
+    const int L = (n + nseg - 1) / nseg;
+
+    const bool two = a.nbuf == 2;
+    long long t = blockIdx.x;
+    if (two && t < ntiles) load_tile<T>(a, f, buf0, t);
+    cp_async_commit();
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+        if (two) {
+            const long long tn = t + gridDim.x;
+            if (tn < ntiles) load_tile<T>(a, f, (it & 1) ? buf0 : buf1, tn);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            load_tile<T>(a, f, buf0, t);
+            cp_async_commit();
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const T* tile = (two && (it & 1)) ? buf1 : buf0;
+        const int chunk = (int)(t % a.nchunks);
+        const long long base = (t / a.nchunks) * a.line_stride;
+        long long vi;
+        int mcol;
+        if (seg < nseg && col_vi(a, chunk, col, &vi, &mcol)) {
+            // displacement of this column in cells
+            const int ia = (int)((vi / a.axis_div) % a.axis_mod);
+            const double c = (a.vmin_a + (ia + 0.5) * a.dv_a) * a.dt_over_h;
+            const bool fwd = c >= 0.0;
+            double ca = fwd ? c : -c;
+            // periodic lines: a shift by whole line lengths is the identity;
+            // walls: the host guarantees ca + 3 <= n. Clamp before the int
+            // conversion.
+            if (!a.wall) ca = fmod(ca, (double)n);
+            if (!(ca <= (double)n)) ca = (double)n;
+            const int s = (int)floor(ca);
+            const T alpha = (T)(ca - s);
+            const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
+            const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+            // value at reversed-frame index j (physical p = j forward, n-1-j reversed)
+            auto fetch = [&](int j) -> T {
+                int p = fwd ? j : n - 1 - j;
+                if (p >= 0 && p < n) return tile[p * ncol + col];
+                if (!a.wall) {
+                    p %= n;
+                    if (p < 0) p += n;
+                    return tile[p * ncol + col];
+                }
+                p = p < 0 ? -1 - p : 2 * n - 1 - p;  // mirror row, v_y -> -v_y column
+                return tile[p * ncol + mcol];
+            };
+            const int k0 = seg * L;
+            const int k1 = min(n, k0 + L);
+            if (k0 < k1) {
+                int j = k0 - s;
+                T fm2 = fetch(j - 2), fm1 = fetch(j - 1), f0 = fetch(j), fp1 = fetch(j + 1);
+                T phim = pfc_phi<T>(alpha, A, B, fm2, fm1, f0);
+                for (int k = k0; k < k1; ++k) {
+                    const T phi = pfc_phi<T>(alpha, A, B, fm1, f0, fp1);
+                    const int i = fwd ? k : n - 1 - k;
+                    f[base + (long long)i * a.row_stride + vi] = f0 - phi + phim;
+                    ++j;
+                    fm2 = fm1;
+                    fm1 = f0;
+                    f0 = fp1;
+                    fp1 = fetch(j + 1);
+                    phim = phi;
+                }
+            }
+        }
+        __syncthreads();  // the buffer of tile t is refilled in a later iteration
+    }
+    cp_async_wait<0>();
+}
+
+static int g_sms = 0;
+
 cudaError_t launch_pfc_space(const SpaceSweepArgs& a, int precision, cudaStream_t st) {
-    size_t es = precision == 64 ? sizeof(double) : sizeof(float);
-    size_t smem = (size_t)a.n * a.ncol * es;
-    dim3 grid(a.nchunks, a.nlines);
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 148;
+    }
+    const size_t es = precision == 64 ? sizeof(double) : sizeof(float);
+    const size_t smem = (size_t)a.nbuf * a.n * a.ncol * es;
+    const long long ntiles = (long long)a.nchunks * a.nlines;
+    // one thread per (column, segment of about 8 cells), up to 1024 threads:
+    // short segments give each SM enough independent sliding windows to hide
+    // the shared-memory latency of the window updates
+    int nseg = (a.n + 7) / 8;
+    if (nseg > 1024 / a.ncol) nseg = 1024 / a.ncol;
+    if (nseg < 1) nseg = 1;
+    const int threads = a.ncol * nseg;
+    int per_sm = 0;
     if (precision == 64) {
         cudaFuncSetAttribute(pfc_space_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        pfc_space_kernel<double><<<grid, 256, smem, st>>>(a);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pfc_space_kernel<double>, threads, smem);
     } else {
         cudaFuncSetAttribute(pfc_space_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        pfc_space_kernel<float><<<grid, 256, smem, st>>>(a);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pfc_space_kernel<float>, threads, smem);
     }
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)g_sms * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (precision == 64) pfc_space_kernel<double><<<(unsigned)grid, threads, smem, st>>>(a);
+    else pfc_space_kernel<float><<<(unsigned)grid, threads, smem, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -17,6 +17,7 @@
 // 32 different lines hits distinct banks.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "block_moments.cuh"
 
 namespace vl {
 
@@ -150,120 +151,88 @@ __device__ __forceinline__ T phi_lim(T alpha, T A, T B, T fm, T f0, T fp) {
     return alpha * (f0 + A * up + B * dn);
 }
 
-// Zero-flux PFC step of one line of N values held in registers, positive
-// displacement s + alpha in the frame where index q runs along `dir`.
-// Writes the new line through `put(position, value)` (positions in the same
-// frame). Everything that would leave through the far boundary piles up in
-// the last cell; cells the profile has left become zero.
-template <typename T, int N, typename Put>
-__device__ __forceinline__ void pfc_line_zero_flux(T (&r)[N], int s, T alpha, Put put) {
-    const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
-    const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
-    T phi_prev = T(0), old_prev = T(0), acc = T(0), phi = T(0);
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        T fp = q + 1 < N ? r[q + 1] : T(0);
-        phi = phi_lim<T>(alpha, A, B, old_prev, r[q], fp);
-        T g = r[q] - phi + phi_prev;
-        phi_prev = phi;
-        old_prev = r[q];
-        r[q] = g;
-    }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        int p = q + s;
-        if (p < N - 1) put(p, r[q]);
-        else acc += r[q];
-    }
-    put(N - 1, acc + phi);
-#pragma unroll
-    for (int p = 0; p < N - 1; ++p)
-        if (p < s) put(p, T(0));
-}
-
 template <int N>
 __device__ __forceinline__ int padded(int i, int j, int k) {
     return (k * N + j) * (N + 1) + i;
 }
 
-// Apply one shear (axis, coefficients in velocity units) to the block in smem.
-template <typename T, int N>
-__device__ void apply_shear(T* blk, const double* sh, const double* vmin, const double* dv) {
-    const int axis = (int)sh[0];
+// Apply one shear along velocity axis AX to the block in smem: every thread
+// owns one line (lo, hi = indices of the lower and higher other axes) and
+// runs the zero-flux PFC step on it in registers. The line is walked in the
+// frame where the displacement is positive (a signed shared-memory stride);
+// everything that would leave through the far boundary piles up in the last
+// cell and cells the profile has left become zero. When no line of the warp
+// moves by a whole cell (the usual case) the shifted write-back reduces to a
+// plain one.
+template <typename T, int N, int AX>
+__device__ __forceinline__ void apply_shear_ax(T* blk, const double* sh, const double* vmin, const double* dv) {
+    constexpr int ST = AX == 0 ? 1 : (AX == 1 ? N + 1 : N * (N + 1));
     const int t = threadIdx.x;
-    if (t >= N * N) return;
-    const int lo = t % N, hi = t / N;  // indices of the lower and higher other axes
-    const int alo = axis == 0 ? 1 : 0, ahi = axis == 2 ? 1 : 2;
+    const bool active = t < N * N;
+    const int lo = active ? t % N : 0, hi = active ? t / N : 0;
+    constexpr int alo = AX == 0 ? 1 : 0, ahi = AX == 2 ? 1 : 2;
+    const int base = AX == 0 ? padded<N>(0, lo, hi) : (AX == 1 ? padded<N>(lo, 0, hi) : padded<N>(lo, hi, 0));
     const T vlo = (T)(vmin[alo] + (lo + 0.5) * dv[alo]);
     const T vhi = (T)(vmin[ahi] + (hi + 0.5) * dv[ahi]);
-    const T inv = (T)(1.0 / dv[axis]);
-    T c = ((T)sh[1] * vlo + (T)sh[2] * vhi + (T)sh[3]) * inv;
+    const T inv = (T)(1.0 / dv[AX]);
+    const T c = ((T)sh[1] * vlo + (T)sh[2] * vhi + (T)sh[3]) * inv;
     const bool fwd = c >= T(0);
     T ca = fwd ? c : -c;
     // beyond N cells everything piles up in the last cell anyway; clamping in
     // floating point also maps NaN to N, so the int conversion is always safe
     if (!(ca < T(N))) ca = T(N);
-    int s = (int)floor(ca);
-    T alpha = ca - (T)s;
-    auto addr = [&](int pos) -> int {
-        if (axis == 0) return padded<N>(pos, lo, hi);
-        if (axis == 1) return padded<N>(lo, pos, hi);
-        return padded<N>(lo, hi, pos);
-    };
+    const int s = (int)floor(ca);
+    const T alpha = ca - (T)s;
+    const int sst = fwd ? ST : -ST;
+    T* line = blk + (fwd ? base : base + (N - 1) * ST);
+    const bool whole = __ballot_sync(0xffffffffu, active && s != 0) != 0u;
+    if (!active) return;
     T r[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) r[q] = blk[addr(fwd ? q : N - 1 - q)];
-    pfc_line_zero_flux<T, N>(r, s, alpha, [&](int p, T v) { blk[addr(fwd ? p : N - 1 - p)] = v; });
+    for (int q = 0; q < N; ++q) r[q] = line[q * sst];
+    const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
+    const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+    T phi_prev = T(0), old_prev = T(0), phi = T(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const T fp = q + 1 < N ? r[q + 1] : T(0);
+        phi = phi_lim<T>(alpha, A, B, old_prev, r[q], fp);
+        const T g = r[q] - phi + phi_prev;
+        phi_prev = phi;
+        old_prev = r[q];
+        r[q] = g;
+    }
+    if (!whole) {
+#pragma unroll
+        for (int q = 0; q < N - 1; ++q) line[q * sst] = r[q];
+        line[(N - 1) * sst] = r[N - 1] + phi;
+        return;
+    }
+    T acc = T(0);
+    T* shifted = line + s * sst;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (q + s < N - 1) shifted[q * sst] = r[q];
+        else acc += r[q];
+    }
+    line[(N - 1) * sst] = acc + phi;
+#pragma unroll
+    for (int p = 0; p < N - 1; ++p)
+        if (p < s) line[p * sst] = T(0);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void apply_shear(T* blk, const double* sh, const double* vmin, const double* dv) {
+    const int axis = (int)sh[0];
+    if (axis == 0) apply_shear_ax<T, N, 0>(blk, sh, vmin, dv);
+    else if (axis == 1) apply_shear_ax<T, N, 1>(blk, sh, vmin, dv);
+    else apply_shear_ax<T, N, 2>(blk, sh, vmin, dv);
 }
 
 // ---------------------------------------------------------------- moments
 
-// Raw moments of the block in smem (padded layout) reduced over the CTA.
-// Line sums over v_x use centred indices (exact in binary floating point);
-// the 20 per-line products are reduced with warp shuffles in T and across
-// warps in FP64 by lanes 0..19 of warp 0, which then expand them to physical
-// velocities with the precomputed binomial table (FP64).
-template <typename T, int N>
-__device__ __forceinline__ void line_products(T (&m)[20], T S0, T S1, T S2, T S3, int j, int k) {
-    const T c = T(0.5) * T(N - 1);
-    T e = T(j) - c, z = T(k) - c;
-    T e2 = e * e, z2 = z * z, ez = e * z;
-    // order: 1 x y z xx xy xz yy yz zz xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
-    m[0] = S0; m[1] = S1; m[2] = e * S0; m[3] = z * S0;
-    m[4] = S2; m[5] = e * S1; m[6] = z * S1; m[7] = e2 * S0; m[8] = ez * S0; m[9] = z2 * S0;
-    m[10] = S3; m[11] = e * S2; m[12] = z * S2; m[13] = e2 * S1; m[14] = ez * S1; m[15] = z2 * S1;
-    m[16] = e2 * e * S0; m[17] = e2 * z * S0; m[18] = e * z2 * S0; m[19] = z2 * z * S0;
-}
-
-template <typename T>
-__device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* out, const MomConv& conv) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int a = 0; a < 20; ++a) {
-        T v = m[a];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        m[a] = v;
-    }
-    const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int a = 0; a < 20; ++a) red[warp * 20 + a] = (double)m[a];
-    __syncthreads();
-    double* im = red + 20 * 32;
-    if (t < 20) {
-        double sacc = 0.0;
-        for (int w = 0; w < nwarp; ++w) sacc += red[w * 20 + t];
-        im[t] = sacc;
-    }
-    __syncwarp();
-    if (t < 20) {
-        double acc = 0.0;
-        for (int q = 0; q < conv.nterm[t]; ++q) acc += conv.coef[t][q] * im[conv.idx[t][q]];
-        out[t] = acc;
-    }
-}
-
+// Raw moments of the block in smem (padded layout) reduced over the CTA
+// (line sums along v_x, see block_moments.cuh).
 template <typename T, int N>
 __device__ void block_moments(const T* blk, double* red, double* out, const MomConv& conv) {
     const int t = threadIdx.x;
@@ -333,6 +302,19 @@ __device__ __forceinline__ void load_block(T* blk, const T* src) {
     }
 }
 
+// asynchronous element copies of one block into the padded layout (the
+// padding breaks 16-byte alignment of the rows, so element-sized copies)
+template <typename T, int N>
+__device__ __forceinline__ void prefetch_block(T* blk, const T* src) {
+    constexpr int V = N * N * N;
+    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+        const int i = e % N, jk = e / N;
+        const unsigned d = (unsigned)__cvta_generic_to_shared(blk + jk * (N + 1) + i);
+        if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + e) : "memory");
+        else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + e) : "memory");
+    }
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void store_block(T* dst, const T* blk) {
     constexpr int V = N * N * N;
@@ -342,16 +324,38 @@ __device__ __forceinline__ void store_block(T* dst, const T* blk) {
     }
 }
 
+// One CTA per velocity block at a time (persistent over cells). With
+// a.nbuf == 2 the next cell's block is copied in while the current one is
+// advected. Registers are capped at 64 per thread (FP32) or 128 (FP64)
+// where the block size allows, so that several CTAs share an SM.
+constexpr int vel_threads(int n) { return ((n * n + 31) / 32) * 32; }
+constexpr int vel_min_blocks(int n, int es) {
+    return 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) > 0 ? 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) : 1;
+}
 template <typename T, int N>
-__global__ void velocity_kernel(VelocityArgs a) {
+__global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) velocity_kernel(VelocityArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* blk = reinterpret_cast<T*>(smem_raw);
-    double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * N * N * (N + 1));
+    constexpr int BLK = N * N * (N + 1);
+    T* const buf0 = reinterpret_cast<T*>(smem_raw);
+    T* const buf1 = buf0 + BLK;
+    double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * BLK * a.nbuf);
     double* sh = red + 20 * 32 + 20;
     T* f = reinterpret_cast<T*>(a.f);
     constexpr long long V = (long long)N * N * N;
-    for (long long cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
-        load_block<T, N>(blk, f + cell * V);
+    const bool two = a.nbuf == 2;
+    long long cell = blockIdx.x;
+    if (two && cell < a.ncell) prefetch_block<T, N>(buf0, f + cell * V);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int it = 0; cell < a.ncell; cell += gridDim.x, ++it) {
+        T* blk = (two && (it & 1)) ? buf1 : buf0;
+        if (two) {
+            const long long nx = cell + gridDim.x;
+            if (nx < a.ncell) prefetch_block<T, N>((it & 1) ? buf0 : buf1, f + nx * V);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            load_block<T, N>(blk, f + cell * V);
+        }
         if (threadIdx.x < 20) sh[threadIdx.x] = a.shears[cell * 20 + threadIdx.x];
         __syncthreads();
         for (int k = 0; k < a.nshear; ++k) {
@@ -362,6 +366,7 @@ __global__ void velocity_kernel(VelocityArgs a) {
         store_block<T, N>(f + cell * V, blk);
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename T, int N>
@@ -454,14 +459,18 @@ static int num_sms() {
 template <typename T, int N>
 static cudaError_t launch_velocity_n(const VelocityArgs& a, cudaStream_t st) {
     const int threads = ((N * N + 31) / 32) * 32;
-    size_t smem = sizeof(T) * N * N * (N + 1) + sizeof(double) * (20 * 32 + 20 + 20);
+    const size_t blk = sizeof(T) * N * N * (N + 1);
+    VelocityArgs b = a;
+    // double buffering while two buffers leave room for two CTAs per SM
+    b.nbuf = 2 * blk <= 100 * 1024 ? 2 : 1;
+    size_t smem = blk * b.nbuf + sizeof(double) * (20 * 32 + 20 + 20);
     cudaFuncSetAttribute(velocity_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<T, N>, threads, smem);
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)num_sms() * per_sm;
     if (grid > a.ncell) grid = a.ncell;
-    velocity_kernel<T, N><<<(unsigned)grid, threads, smem, st>>>(a);
+    velocity_kernel<T, N><<<(unsigned)grid, threads, smem, st>>>(b);
     count_launch();
     return cudaGetLastError();
 }
