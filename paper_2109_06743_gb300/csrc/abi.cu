@@ -257,6 +257,8 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
         const long long run = wall ? a.nvx : V;
         a.vec = (run * es) % 16 == 0 && ((long long)a.ncol * es) % 16 == 0 && (V * es) % 16 == 0;
     }
+    if ((long long)a.nchunks * a.nlines >= (1LL << 31) - (1LL << 20))
+        return fail(ctx, VL_ENOTSUP, "too many sweep tiles (%d x %d)", a.nchunks, a.nlines);
     const size_t tile_bytes = (size_t)a.n * a.ncol * es;
     a.nbuf = 2 * tile_bytes <= 200 * 1024 ? 2 : 1;
     if (tile_bytes > 200 * 1024 || a.ncol > 256)

@@ -139,6 +139,9 @@ __device__ void maxwellian_line_params(const double* k, bool valid, const double
     par[9] = L;
 }
 
+// one thread per (cell, fit); the parameters are stored in the precision of
+// f (T), packed [ncell][2][kPar] at the start of a.par
+template <typename T>
 __global__ void exchange_params_kernel(ExchangeArgs a) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (g >= 2 * a.ncell) return;
@@ -146,8 +149,11 @@ __global__ void exchange_params_kernel(ExchangeArgs a) {
     const int w = (int)(g & 1);
     const int stv = a.status[cell * 2], stf = a.status[cell * 2 + 1];
     const bool valid = stv != 2 && stf != 2;
-    maxwellian_line_params((w == 0 ? a.coef_v : a.coef_f) + cell * kCoef, valid, a.vmin, a.dv,
-                           a.par + cell * 2 * kPar + w * kPar);
+    double par[kPar];
+    maxwellian_line_params((w == 0 ? a.coef_v : a.coef_f) + cell * kCoef, valid, a.vmin, a.dv, par);
+    T* out = reinterpret_cast<T*>(a.par) + cell * 2 * kPar + w * kPar;
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) out[q] = (T)par[q];
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -160,15 +166,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // FP32: per element, exponent in base 2 and ex2.approx (relative error
 // about 2^-22).
 template <int N>
-__device__ __forceinline__ void add_maxwellian(float (&r)[N], const double* pd, int i, int j, float sgn,
+__device__ __forceinline__ void add_maxwellian(float (&r)[N], const float* pd, int i, int j, float sgn,
                                                const double*) {
-    const float hz = (float)pd[8];
+    const float hz = pd[8];
     if (!(hz > 0.f)) return;
     constexpr float kLog2e = 1.4426950408889634f;
-    const float dx = (float)i - (float)pd[0], dy = (float)j - (float)pd[1];
-    const float Q = (float)pd[3] * dx * dx + 2.f * (float)pd[4] * dx * dy + (float)pd[5] * dy * dy;
-    const float kc = (float)pd[2] + (float)pd[6] * dx + (float)pd[7] * dy;
-    const float Ec2 = ((float)pd[9] - 0.5f * Q) * kLog2e;
+    const float dx = (float)i - pd[0], dy = (float)j - pd[1];
+    const float Q = pd[3] * dx * dx + 2.f * pd[4] * dx * dy + pd[5] * dy * dy;
+    const float kc = pd[2] + pd[6] * dx + pd[7] * dy;
+    const float Ec2 = (pd[9] - 0.5f * Q) * kLog2e;
     const float hz2 = hz * kLog2e;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -224,9 +230,9 @@ constexpr int ex_threads(int n) { return ((n * n + 31) / 32) * 32; }
 template <typename T, int N>
 __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a) {
     __shared__ double red[20 * 32 + 20];
-    __shared__ double ssum[32];
+    __shared__ T ssum[32];
     __shared__ int sneg[32];
-    __shared__ double spar[2 * kPar];
+    __shared__ T spar[2 * kPar];
     __shared__ double gtab[2][sizeof(T) == 8 ? 2 * N - 1 : 1];
     T* f = reinterpret_cast<T*>(a.f);
     constexpr long long V = (long long)N * N * N;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
     const int lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
     const bool active = t < NN;
     const int i = active ? t % N : 0, j = active ? t / N : 0;
-    const double vol = a.dv[0] * a.dv[1] * a.dv[2];
+    const T* par = reinterpret_cast<const T*>(a.par);
     for (long long cell = blockIdx.x; cell < a.ncell; cell += gridDim.x) {
         T r[N];
         const T* src = f + cell * V + t;
@@ -245,10 +251,10 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
         }
         const int stv = a.status[cell * 2], stf = a.status[cell * 2 + 1];
         const bool skip = (stv == 2 || stf == 2);
-        if (t < 2 * kPar) spar[t] = a.par[cell * 2 * kPar + t];
+        if (t < 2 * kPar) spar[t] = par[cell * 2 * kPar + t];
         if (sizeof(T) == 8 && t < 2 * (2 * N - 1)) {
             const int w = t / (2 * N - 1), m = t % (2 * N - 1) - (N - 1);
-            const double hz = a.par[cell * 2 * kPar + w * kPar + 8];
+            const double hz = (double)par[cell * 2 * kPar + w * kPar + 8];
             gtab[w][sizeof(T) == 8 ? t % (2 * N - 1) : 0] = exp(-hz * (double)(m * m));
         }
         __syncthreads();
@@ -263,22 +269,24 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
                 lsum += fmax(r[k], T(0));
             }
         }
-        // block reduction: any negative, sum of the clipped values
-        double s = warp_sum((double)lsum);
-        int nn = __any_sync(0xffffffffu, neg);
+        // block reduction: any negative; per-warp sums of the clipped values
+        // (partial sums in T, then FP64 across warps in the rare clipped case)
+        T ls = lsum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+        const int nn = __any_sync(0xffffffffu, neg);
         if (lane == 0) {
-            ssum[warp] = s;
+            ssum[warp] = ls;
             sneg[warp] = nn;
         }
         __syncthreads();
-        double tot = 0.0;
         int anyneg = 0;
-        for (int w = 0; w < nwarp; ++w) {
-            tot += ssum[w];
-            anyneg |= sneg[w];
-        }
+        for (int w = 0; w < nwarp; ++w) anyneg |= sneg[w];
         T scale = T(1);
         if (anyneg && !skip) {
+            double tot = 0.0;
+            for (int w = 0; w < nwarp; ++w) tot += (double)ssum[w];
+            const double vol = a.dv[0] * a.dv[1] * a.dv[2];
             const double nV = a.vmom[cell * 20];
             scale = (T)(tot > 0.0 ? nV / (tot * vol) : 0.0);
             if (t == 0) atomicAdd(&a.counters[CNT_CLIPPED], 1ull);
@@ -494,7 +502,7 @@ template <typename T, int N>
 static cudaError_t launch_exchange_n(const ExchangeArgs& a, cudaStream_t st) {
     {
         const long long n = 2 * a.ncell;
-        exchange_params_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+        exchange_params_kernel<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -39,9 +39,9 @@ template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
 
 // velocity index of tile column col, and the column holding its v_y mirror
-__device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int col, long long* vi, int* mcol) {
+__device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int col, int* vi, int* mcol) {
     if (a.mode == 0) {
-        long long v = (long long)chunk * a.ncol + col;
+        const int v = chunk * a.ncol + col;
         *vi = v;
         *mcol = col;
         return v < a.V;
@@ -50,12 +50,12 @@ __device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int c
     const int k = chunk / half, j = chunk % half;
     const int jm = a.nvy - 1 - j;
     if (col < a.nvx) {
-        *vi = ((long long)k * a.nvy + j) * a.nvx + col;
+        *vi = (k * a.nvy + j) * a.nvx + col;
         *mcol = (jm == j) ? col : col + a.nvx;
         return true;
     }
     if (jm == j || col >= 2 * a.nvx) return false;
-    *vi = ((long long)k * a.nvy + jm) * a.nvx + (col - a.nvx);
+    *vi = (k * a.nvy + jm) * a.nvx + (col - a.nvx);
     *mcol = col - a.nvx;
     return true;
 }
@@ -64,10 +64,10 @@ __device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int c
 // run starts on a 16-byte boundary and spans a multiple of 16 bytes (a.vec),
 // else plain element loads
 template <typename T>
-__device__ __forceinline__ void load_tile(const SpaceSweepArgs& a, const T* f, T* tile, long long tidx) {
-    const int chunk = (int)(tidx % a.nchunks);
-    const long long base = (tidx / a.nchunks) * a.line_stride;
-    long long vi;
+__device__ __forceinline__ void load_tile(const SpaceSweepArgs& a, const T* f, T* tile, int tidx) {
+    const int chunk = tidx % a.nchunks;
+    const long long base = (long long)(tidx / a.nchunks) * a.line_stride;
+    int vi;
     int mc;
     if (a.vec) {
         constexpr int per = 16 / sizeof(T);
@@ -85,6 +85,14 @@ __device__ __forceinline__ void load_tile(const SpaceSweepArgs& a, const T* f, T
     }
 }
 
+// Per-column constants of the update, one entry per velocity index along the
+// sweep axis (computed once per CTA in FP64, used in T)
+template <typename T>
+struct ColumnStep {
+    T alpha, A, B;
+    int s, fwd;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(1024) pfc_space_kernel(SpaceSweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -92,19 +100,40 @@ __global__ void __launch_bounds__(1024) pfc_space_kernel(SpaceSweepArgs a) {
     const int ncol = a.ncol, n = a.n;
     T* const buf0 = reinterpret_cast<T*>(smem_raw);
     T* const buf1 = buf0 + (size_t)n * ncol;
-    const long long ntiles = (long long)a.nchunks * a.nlines;
+    ColumnStep<T>* steps = reinterpret_cast<ColumnStep<T>*>(smem_raw + (size_t)a.nbuf * n * ncol * sizeof(T));
+    for (int ia = threadIdx.x; ia < a.axis_mod; ia += blockDim.x) {
+        // displacement of velocity index ia in cells
+        const double c = (a.vmin_a + (ia + 0.5) * a.dv_a) * a.dt_over_h;
+        const bool fwd = c >= 0.0;
+        double ca = fwd ? c : -c;
+        // periodic lines: a shift by whole line lengths is the identity;
+        // walls: the host guarantees ca + 3 <= n. Clamp before the int
+        // conversion.
+        if (!a.wall) ca = fmod(ca, (double)n);
+        if (!(ca <= (double)n)) ca = (double)n;
+        const int s = (int)floor(ca);
+        const T alpha = (T)(ca - s);
+        ColumnStep<T> cs;
+        cs.alpha = alpha;
+        cs.A = (T(1) - alpha) * (T(2) - alpha) / T(6);
+        cs.B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+        cs.s = s;
+        cs.fwd = fwd;
+        steps[ia] = cs;
+    }
+    const int ntiles = a.nchunks * a.nlines;  // < 2^31, checked on the host
     const int nseg = blockDim.x / ncol;
     const int col = threadIdx.x % ncol;
     const int seg = threadIdx.x / ncol;
     const int L = (n + nseg - 1) / nseg;
 
     const bool two = a.nbuf == 2;
-    long long t = blockIdx.x;
+    int t = blockIdx.x;
     if (two && t < ntiles) load_tile<T>(a, f, buf0, t);
     cp_async_commit();
     for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
         if (two) {
-            const long long tn = t + gridDim.x;
+            const int tn = t + gridDim.x;
             if (tn < ntiles) load_tile<T>(a, f, (it & 1) ? buf0 : buf1, tn);
             cp_async_commit();
             cp_async_wait<1>();
@@ -115,25 +144,15 @@ __global__ void __launch_bounds__(1024) pfc_space_kernel(SpaceSweepArgs a) {
         }
         __syncthreads();
         const T* tile = (two && (it & 1)) ? buf1 : buf0;
-        const int chunk = (int)(t % a.nchunks);
-        const long long base = (t / a.nchunks) * a.line_stride;
-        long long vi;
+        const int chunk = t % a.nchunks;
+        const long long base = (long long)(t / a.nchunks) * a.line_stride;
+        int vi;
         int mcol;
         if (seg < nseg && col_vi(a, chunk, col, &vi, &mcol)) {
-            // displacement of this column in cells
-            const int ia = (int)((vi / a.axis_div) % a.axis_mod);
-            const double c = (a.vmin_a + (ia + 0.5) * a.dv_a) * a.dt_over_h;
-            const bool fwd = c >= 0.0;
-            double ca = fwd ? c : -c;
-            // periodic lines: a shift by whole line lengths is the identity;
-            // walls: the host guarantees ca + 3 <= n. Clamp before the int
-            // conversion.
-            if (!a.wall) ca = fmod(ca, (double)n);
-            if (!(ca <= (double)n)) ca = (double)n;
-            const int s = (int)floor(ca);
-            const T alpha = (T)(ca - s);
-            const T A = (T(1) - alpha) * (T(2) - alpha) / T(6);
-            const T B = (T(1) - alpha) * (T(1) + alpha) / T(6);
+            const ColumnStep<T> cs = steps[(vi / a.axis_div) % a.axis_mod];
+            const bool fwd = cs.fwd != 0;
+            const int s = cs.s;
+            const T alpha = cs.alpha, A = cs.A, B = cs.B;
             // value at reversed-frame index j (physical p = j forward, n-1-j reversed)
             auto fetch = [&](int j) -> T {
                 int p = fwd ? j : n - 1 - j;
@@ -180,12 +199,12 @@ cudaError_t launch_pfc_space(const SpaceSweepArgs& a, int precision, cudaStream_
         if (g_sms <= 0) g_sms = 148;
     }
     const size_t es = precision == 64 ? sizeof(double) : sizeof(float);
-    const size_t smem = (size_t)a.nbuf * a.n * a.ncol * es;
+    const size_t smem = (size_t)a.nbuf * a.n * a.ncol * es + (size_t)a.axis_mod * (es == 8 ? sizeof(ColumnStep<double>) : sizeof(ColumnStep<float>));
     const long long ntiles = (long long)a.nchunks * a.nlines;
-    // one thread per (column, segment of about 8 cells), up to 1024 threads:
+    // one thread per (column, segment of about 16 cells), up to 1024 threads:
     // short segments give each SM enough independent sliding windows to hide
     // the shared-memory latency of the window updates
-    int nseg = (a.n + 7) / 8;
+    int nseg = (a.n + 15) / 16;
     if (nseg > 1024 / a.ncol) nseg = 1024 / a.ncol;
     if (nseg < 1) nseg = 1;
     const int threads = a.ncol * nseg;

@@ -165,17 +165,15 @@ __device__ __forceinline__ int padded(int i, int j, int k) {
 // moves by a whole cell (the usual case) the shifted write-back reduces to a
 // plain one.
 template <typename T, int N, int AX>
-__device__ __forceinline__ void apply_shear_ax(T* blk, const double* sh, const double* vmin, const double* dv) {
+__device__ __forceinline__ void apply_shear_ax(T* blk, const T* sh, const T* vc, const T* inv_dv) {
     constexpr int ST = AX == 0 ? 1 : (AX == 1 ? N + 1 : N * (N + 1));
     const int t = threadIdx.x;
     const bool active = t < N * N;
     const int lo = active ? t % N : 0, hi = active ? t / N : 0;
     constexpr int alo = AX == 0 ? 1 : 0, ahi = AX == 2 ? 1 : 2;
     const int base = AX == 0 ? padded<N>(0, lo, hi) : (AX == 1 ? padded<N>(lo, 0, hi) : padded<N>(lo, hi, 0));
-    const T vlo = (T)(vmin[alo] + (lo + 0.5) * dv[alo]);
-    const T vhi = (T)(vmin[ahi] + (hi + 0.5) * dv[ahi]);
-    const T inv = (T)(1.0 / dv[AX]);
-    const T c = ((T)sh[1] * vlo + (T)sh[2] * vhi + (T)sh[3]) * inv;
+    const T vlo = vc[alo * N + lo], vhi = vc[ahi * N + hi];
+    const T c = (sh[1] * vlo + sh[2] * vhi + sh[3]) * inv_dv[AX];
     const bool fwd = c >= T(0);
     T ca = fwd ? c : -c;
     // beyond N cells everything piles up in the last cell anyway; clamping in
@@ -221,12 +219,14 @@ __device__ __forceinline__ void apply_shear_ax(T* blk, const double* sh, const d
         if (p < s) line[p * sst] = T(0);
 }
 
+// sh: (axis, c_lo, c_hi, c_0) in T; vc[3][N]: cell-centre velocities;
+// inv_dv[3]: 1 / dv
 template <typename T, int N>
-__device__ __forceinline__ void apply_shear(T* blk, const double* sh, const double* vmin, const double* dv) {
+__device__ __forceinline__ void apply_shear(T* blk, const T* sh, const T* vc, const T* inv_dv) {
     const int axis = (int)sh[0];
-    if (axis == 0) apply_shear_ax<T, N, 0>(blk, sh, vmin, dv);
-    else if (axis == 1) apply_shear_ax<T, N, 1>(blk, sh, vmin, dv);
-    else apply_shear_ax<T, N, 2>(blk, sh, vmin, dv);
+    if (axis == 0) apply_shear_ax<T, N, 0>(blk, sh, vc, inv_dv);
+    else if (axis == 1) apply_shear_ax<T, N, 1>(blk, sh, vc, inv_dv);
+    else apply_shear_ax<T, N, 2>(blk, sh, vc, inv_dv);
 }
 
 // ---------------------------------------------------------------- moments
@@ -339,10 +339,17 @@ __global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) 
     T* const buf0 = reinterpret_cast<T*>(smem_raw);
     T* const buf1 = buf0 + BLK;
     double* red = reinterpret_cast<double*>(smem_raw + sizeof(T) * BLK * a.nbuf);
-    double* sh = red + 20 * 32 + 20;
+    T* sh = reinterpret_cast<T*>(red + 20 * 32 + 20);  // [20] shears of the cell
+    T* vc = sh + 20;                                    // [3][N] cell-centre velocities
+    T* inv_dv = vc + 3 * N;                             // [3]
     T* f = reinterpret_cast<T*>(a.f);
     constexpr long long V = (long long)N * N * N;
     const bool two = a.nbuf == 2;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        const int ax = q / N, i = q % N;
+        vc[q] = (T)(a.vmin[ax] + (i + 0.5) * a.dv[ax]);
+    }
+    if (threadIdx.x < 3) inv_dv[threadIdx.x] = (T)(1.0 / a.dv[threadIdx.x]);
     long long cell = blockIdx.x;
     if (two && cell < a.ncell) prefetch_block<T, N>(buf0, f + cell * V);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -356,10 +363,10 @@ __global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) 
         } else {
             load_block<T, N>(blk, f + cell * V);
         }
-        if (threadIdx.x < 20) sh[threadIdx.x] = a.shears[cell * 20 + threadIdx.x];
+        if (threadIdx.x < 20) sh[threadIdx.x] = (T)a.shears[cell * 20 + threadIdx.x];
         __syncthreads();
         for (int k = 0; k < a.nshear; ++k) {
-            apply_shear<T, N>(blk, sh + 4 * k, a.vmin, a.dv);
+            apply_shear<T, N>(blk, sh + 4 * k, vc, inv_dv);
             __syncthreads();
         }
         if (a.mom_out) block_moments<T, N>(blk, red, a.mom_out + cell * 20, a.conv);
@@ -463,7 +470,7 @@ static cudaError_t launch_velocity_n(const VelocityArgs& a, cudaStream_t st) {
     VelocityArgs b = a;
     // double buffering while two buffers leave room for two CTAs per SM
     b.nbuf = 2 * blk <= 100 * 1024 ? 2 : 1;
-    size_t smem = blk * b.nbuf + sizeof(double) * (20 * 32 + 20 + 20);
+    size_t smem = blk * b.nbuf + sizeof(double) * (20 * 32 + 20) + sizeof(T) * (20 + 3 * N + 3);
     cudaFuncSetAttribute(velocity_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<T, N>, threads, smem);
