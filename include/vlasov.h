@@ -111,6 +111,30 @@ vl_status pfc_advect_x(vl_ctx* ctx, int species, int axis, double dt, vl_stream_
 vl_status pfc_advect_v(vl_ctx* ctx, int species, double dt, double* mom_out,
                        vl_stream_t stream);
 
+/* pfc_advect_v without a context or workspace: the same velocity pass for
+ * `ncell` consecutive cells given by plain device pointers, with its per-cell
+ * scratch (20 doubles per cell: the shear factors of the velocity map) in a
+ * fixed static device array of the library instead of a caller workspace.
+ * It allocates no memory, host or device. The paper has no counterpart: it
+ * serves callers that may not allocate device memory (hosts that own every
+ * device byte through an arena fixed before the run; latency-bound callers
+ * for which an allocation or its failure mid-step is not acceptable).
+ *   desc      validated like vlasov_init's; species s selects q, m and the box
+ *   f_dev     [ncell][V] species-s velocity blocks in desc->precision, in place
+ *   eb_dev    [ncell][6] double, cell-centred E and B of those cells
+ *   mom_out   [ncell][20] raw moments of the result, or NULL
+ * At most VL_STATIC_SCRATCH_CELLS cells per call (VL_EINVAL beyond that:
+ * split the call by cell ranges); ncell == 0 does nothing. The first call on
+ * each device resolves the array's address (a runtime query, not a stream
+ * operation) with that device current; make it before any stream capture.
+ * Every call shares the array: nothing in it has to start at zero (each call
+ * writes every row it reads), but calls that overlap in time on one device
+ * race on it. Errors are reported through vl_last_error(NULL). */
+#define VL_STATIC_SCRATCH_CELLS 32768
+vl_status pfc_advect_v_static(const vl_desc* desc, int species, void* f_dev,
+                              const double* eb_dev, long long ncell, double dt,
+                              double* mom_out, vl_stream_t stream);
+
 /* Raw midpoint moments of species s (Sec. 2.1), [ncell][20] (1D1V: [ncell][4]). */
 vl_status moments(vl_ctx* ctx, int species, double* mom_out, vl_stream_t stream);
 

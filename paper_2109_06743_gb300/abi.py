@@ -17,7 +17,7 @@ MAX_SPECIES = 4
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
-            "pfc_advect_v", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
+            "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
             "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count"]
 
 
@@ -75,6 +75,7 @@ def lib():
     L.vl_last_error.restype = ctypes.c_char_p
     L.pfc_advect_x.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp]
     L.pfc_advect_v.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp]
+    L.pfc_advect_v_static.argtypes = [D, ctypes.c_int, _vp, _vp, ctypes.c_longlong, ctypes.c_double, _vp, _vp]
     L.moments.argtypes = [_vp, ctypes.c_int, _vp, _vp]
     L.moment_fit.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.moment_fit_solve.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]
@@ -166,6 +167,16 @@ def pfc_advect_x(ctx, species, axis, dt, stream=None):
 
 def pfc_advect_v(ctx, species, dt, mom_out=None, stream=None):
     _check(ctx, lib().pfc_advect_v(ctx, species, dt, ptr(mom_out), stream_handle(stream)))
+
+
+STATIC_SCRATCH_CELLS = 32768  # VL_STATIC_SCRATCH_CELLS
+
+
+def pfc_advect_v_static(desc, species, f, eb, ncell, dt, mom_out=None, stream=None):
+    """Context-free velocity pass on `ncell` cells with the library's static
+    scratch (no allocation); errors come from vl_last_error(NULL)."""
+    _check(None, lib().pfc_advect_v_static(ctypes.byref(desc), species, ptr(f), ptr(eb), int(ncell), dt,
+                                           ptr(mom_out), stream_handle(stream)))
 
 
 def moments(ctx, species, mom_out, stream=None):

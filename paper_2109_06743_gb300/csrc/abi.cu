@@ -286,6 +286,39 @@ vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream
     return cuda_check(ctx, vl::launch_velocity(a, d.nvdim, d.precision, (cudaStream_t)stream), "pfc_advect_v");
 }
 
+vl_status pfc_advect_v_static(const vl_desc* desc, int s, void* f_dev, const double* eb_dev, long long ncell,
+                              double dt, double* mom_out, vl_stream_t stream) {
+    vl_status st = validate(desc, nullptr);
+    if (st != VL_OK) return st;
+    const vl_desc& d = *desc;
+    if (s < 0 || s >= d.nspecies) return fail(nullptr, VL_EINVAL, "species %d out of range", s);
+    if (ncell < 0) return fail(nullptr, VL_EINVAL, "ncell must be >= 0 (got %lld)", ncell);
+    if (ncell > VL_STATIC_SCRATCH_CELLS)
+        return fail(nullptr, VL_EINVAL,
+                    "pfc_advect_v_static: %lld cells exceed the static scratch (%d cells); split the call",
+                    ncell, VL_STATIC_SCRATCH_CELLS);
+    if (ncell == 0) return VL_OK;
+    if (!f_dev || !eb_dev) return fail(nullptr, VL_EINVAL, "f_dev and eb_dev are required");
+    if (!std::isfinite(dt)) return fail(nullptr, VL_EINVAL, "dt is not finite");
+    void* scratch = nullptr;
+    st = cuda_check(nullptr, vl::static_scratch_address(&scratch), "pfc_advect_v_static (scratch address)");
+    if (st != VL_OK) return st;
+    vl::VelocityArgs a;
+    a.f = f_dev;
+    a.eb = eb_dev;
+    a.shears = static_cast<double*>(scratch);
+    a.mom_out = mom_out;
+    a.ncell = ncell;
+    a.nv = d.nv[s][0];
+    a.nshear = d.nshear;
+    a.qm = d.q[s] / d.m[s];
+    a.dt = dt;
+    fill_box(d, s, a.vmin, a.dv);
+    vl::make_mom_conv(a.vmin, a.dv, d.nv[s][0], &a.conv);
+    return cuda_check(nullptr, vl::launch_velocity(a, d.nvdim, d.precision, (cudaStream_t)stream),
+                      "pfc_advect_v_static");
+}
+
 vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;

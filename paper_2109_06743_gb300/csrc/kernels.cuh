@@ -48,6 +48,8 @@ struct VelocityArgs {
     MomConv conv;
 };
 cudaError_t launch_velocity(const VelocityArgs& a, int nvdim, int precision, cudaStream_t st);
+// address of the static scratch of pfc_advect_v_static on the current device
+cudaError_t static_scratch_address(void** out);
 
 struct MomentArgs {
     const void* f;
