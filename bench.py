@@ -111,6 +111,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# FP32-pipe operations (add, multiply or fused multiply-add: one each) per
+# velocity cell of one evaluation in the double-float Newton fit: moments of
+# degree <= 2 (two double-float products for the recurrence, three
+# compensated accumulations, the index step), plus the FP32 sums of degree
+# <= 4 when the Jacobian is formed in the same pass. Derived operation by
+# operation in the design doc.
+OPS_MOMENT_EVAL = 46
+OPS_GRAM_EVAL = 7
+# DRAM bytes per fitted cell (both fits) of newton_kernel, from the ncu
+# capture summarised in profiles/newton_kernel_harris_128x64_v20.md; None
+# until a capture of the current kernel exists.
+NEWTON_DRAM_BYTES_PER_CELL = None
+
+
+def alu_peak_tops():
+    """FP32-pipe peak from the unit counts and clock: 152 SMs x 128 FP32
+    lanes x the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    return 152 * 128 * mhz * 1e6 / 1e12
+
+
+def newton_roofline(cfg, stats, fit_ms, launches):
+    """ALU roofline of the Newton fit kernel over the timed region: the
+    algorithmic FP32-pipe operations (device counters of the evaluations x
+    velocity cells x operations per cell) over the kernel's CUDA-event time."""
+    if not fit_ms:
+        return None
+    n3 = cfg.species[0].nv[0] ** 3
+    ops = (OPS_MOMENT_EVAL * (stats[4] + stats[6]) + OPS_GRAM_EVAL * (stats[5] + stats[7])) * n3
+    achieved = ops / (fit_ms / 1e3) / 1e12
+    peak = alu_peak_tops()
+    traffic = None
+    if NEWTON_DRAM_BYTES_PER_CELL is not None:
+        traffic = NEWTON_DRAM_BYTES_PER_CELL * cfg.ncell
+    return {"kernel": "fit_solve (newton_kernel)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "Tops/s (FP32 pipe)", "frac": achieved / peak, "traffic": traffic,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+            "ops_per_launch": ops / max(1, launches),
+            "evaluations": {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7]}}
+
+
 def cpu_baseline(steps=1, sample=(32, 16)):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     a 32x16 spatial subdomain with the workload's dx, dv (both species),
@@ -254,14 +299,13 @@ def main():
             avg_s = phase_ms[ph] / count[ph] / 1e3
             rows[ph] = {"ms_per_launch": avg_s * 1e3, "GBps": b * per_launch_cells / avg_s / 1e9,
                         "frac_of_%s_hbm" % peak_kind: b * per_launch_cells / avg_s / 1e9 / peak}
+    newton = newton_roofline(cfg, stats, phase_ms.get("fit_solve"), count.get("fit_solve", 1))
     if dom in hbm_phases:
         roof = {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["GBps"], "peak": peak, "unit": "GB/s",
                 "frac": rows[dom]["GBps"] / peak, "traffic": None, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": 8 * per_launch_cells}
     else:
-        # FP64 Newton fit: bounded by the FP64 pipe (measured 1.2 TFLOP/s on GB300)
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": 1.2, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "note": "FP64 Newton fit; see DESIGN.md for its operation count"}
+        roof = newton
 
     # ---- end to end through the public API with host buffers ------------------
     e2e = None

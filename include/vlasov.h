@@ -182,8 +182,14 @@ vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom,
 
 /* Device counters accumulated since the last reset: out[0] Newton
  * iterations, out[1] Newton fallbacks, out[2] clipped cells, out[3] cells
- * with non-finite or non-positive targets. Synchronises the stream. */
-vl_status vl_read_stats(vl_ctx* ctx, long long out[4], vl_stream_t stream);
+ * with non-finite or non-positive targets; the work of the 2D3V Newton fits
+ * (each counted once per fit and evaluation, over the whole velocity block):
+ * out[4] double-float moment evaluations (recurrence path), out[5] FP32
+ * Jacobian (Gram) evaluations, out[6] evaluations with one FP64 exponential
+ * per velocity cell (wide exponent range), out[7] Newton steps with the
+ * FP64 Jacobian. Synchronises the stream. */
+#define VL_NSTATS 8
+vl_status vl_read_stats(vl_ctx* ctx, long long out[VL_NSTATS], vl_stream_t stream);
 vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream);
 
 /* Number of kernels this library has launched (all contexts, process-wide). */

@@ -13,6 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvlasov.so")
 MAX_SPECIES = 4
+NSTATS = 8  # VL_NSTATS
 
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
@@ -207,7 +208,7 @@ def maxwell_step(ctx, h, mom=None, stream=None):
 
 
 def vl_read_stats(ctx, stream=None):
-    out = (ctypes.c_longlong * 4)()
+    out = (ctypes.c_longlong * NSTATS)()
     _check(ctx, lib().vl_read_stats(ctx, out, stream_handle(stream)))
     return list(out)
 

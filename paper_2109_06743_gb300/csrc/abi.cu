@@ -67,7 +67,7 @@ Layout layout_of(const vl_desc& d) {
     L.u1 = off; off = align256(off + nc * 10 * sizeof(double));
     L.u2 = off; off = align256(off + nc * 10 * sizeof(double));
     L.cur = off; off = align256(off + nc * 3 * sizeof(double));
-    L.counters = off; off = align256(off + 4 * sizeof(unsigned long long));
+    L.counters = off; off = align256(off + VL_NSTATS * sizeof(unsigned long long));
     L.total = off;
     return L;
 }
@@ -179,7 +179,7 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
         vl::make_mom_conv(vmin, dv, desc->nv[s][0], &c->conv[s]);
     }
     c->err[0] = 0;
-    cudaError_t e = cudaMemset(c->ws.counters, 0, 4 * sizeof(unsigned long long));
+    cudaError_t e = cudaMemset(c->ws.counters, 0, VL_NSTATS * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         delete c;
         return fail(nullptr, VL_ECUDA, "clearing counters: %s", cudaGetErrorString(e));
@@ -473,20 +473,20 @@ vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_strea
     return cuda_check(ctx, vl::launch_maxwell(a, cs), "maxwell_step (FDTD)");
 }
 
-vl_status vl_read_stats(vl_ctx* ctx, long long out[4], vl_stream_t stream) {
+vl_status vl_read_stats(vl_ctx* ctx, long long out[VL_NSTATS], vl_stream_t stream) {
     if (!ctx || !out) return fail(ctx, VL_EINVAL, "NULL argument");
-    unsigned long long h[4];
+    unsigned long long h[VL_NSTATS];
     cudaStream_t cs = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(h, ctx->ws.counters, sizeof(h), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return cuda_check(ctx, e, "vl_read_stats");
-    for (int q = 0; q < 4; ++q) out[q] = (long long)h[q];
+    for (int q = 0; q < VL_NSTATS; ++q) out[q] = (long long)h[q];
     return VL_OK;
 }
 
 vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream) {
     if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
-    return cuda_check(ctx, cudaMemsetAsync(ctx->ws.counters, 0, 4 * sizeof(unsigned long long), (cudaStream_t)stream),
+    return cuda_check(ctx, cudaMemsetAsync(ctx->ws.counters, 0, VL_NSTATS * sizeof(unsigned long long), (cudaStream_t)stream),
                       "vl_reset_stats");
 }
 

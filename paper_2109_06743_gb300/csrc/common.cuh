@@ -40,7 +40,7 @@ struct Workspace {
     double* fluid_u2;     // [ncell][10]
     double* fluid_l;      // [ncell][10]
     double* cur;          // [ncell][3] current density at cell centres
-    unsigned long long* counters;  // [4]
+    unsigned long long* counters;  // [VL_NSTATS]
     float* mlp;           // MLP weights and scratch
 };
 
