@@ -414,6 +414,7 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
         a.bc_y = d.bc_y;
         a.nvdim = d.nvdim;
         a.nmom = nmom;
+        a.precision = d.precision;
         a.dx = d.dx;
         a.dy = d.dy;
         a.qm = d.q[s] / d.m[s];

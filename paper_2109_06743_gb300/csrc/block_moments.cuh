@@ -40,7 +40,11 @@ __device__ __forceinline__ void line_products_z(T (&m)[20], T S0, T S1, T S2, T 
 }
 
 // reduce the per-thread products over the CTA and write the 20 physical
-// raw moments to out (uses red[20 * 32 + 20]; contains a __syncthreads)
+// raw moments to out (uses red[20 * 32 + 20]; contains a __syncthreads).
+// Warp partial sums are combined in T by lanes 0..19 of warp 0; only the
+// final binomial expansion runs in FP64 (on GB300 an FP64 warp instruction
+// occupies the pipe for many cycles however few lanes are active, so FP64
+// work stays on one warp).
 template <typename T>
 __device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* out, const MomConv& conv) {
     const int t = threadIdx.x;
@@ -52,15 +56,16 @@ __device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* 
         m[a] = v;
     }
     const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
+    T* part = reinterpret_cast<T*>(red);
     if (lane == 0)
 #pragma unroll
-        for (int a = 0; a < 20; ++a) red[warp * 20 + a] = (double)m[a];
+        for (int a = 0; a < 20; ++a) part[warp * 20 + a] = m[a];
     __syncthreads();
     double* im = red + 20 * 32;
     if (t < 20) {
-        double sacc = 0.0;
-        for (int w = 0; w < nwarp; ++w) sacc += red[w * 20 + t];
-        im[t] = sacc;
+        T sacc = T(0);
+        for (int w = 0; w < nwarp; ++w) sacc += part[w * 20 + t];
+        im[t] = (double)sacc;
     }
     __syncwarp();
     if (t < 20) {

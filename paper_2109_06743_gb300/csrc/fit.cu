@@ -231,6 +231,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a) {
     __shared__ double red[20 * 32 + 20];
     __shared__ T ssum[32];
+    __shared__ T sscale;
     __shared__ int sneg[32];
     __shared__ T spar[2 * kPar];
     __shared__ double gtab[2][sizeof(T) == 8 ? 2 * N - 1 : 1];
@@ -284,12 +285,17 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
         for (int w = 0; w < nwarp; ++w) anyneg |= sneg[w];
         T scale = T(1);
         if (anyneg && !skip) {
-            double tot = 0.0;
-            for (int w = 0; w < nwarp; ++w) tot += (double)ssum[w];
-            const double vol = a.dv[0] * a.dv[1] * a.dv[2];
-            const double nV = a.vmom[cell * 20];
-            scale = (T)(tot > 0.0 ? nV / (tot * vol) : 0.0);
-            if (t == 0) atomicAdd(&a.counters[CNT_CLIPPED], 1ull);
+            // one thread forms the rescale factor in FP64
+            if (t == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < nwarp; ++w) tot += (double)ssum[w];
+                const double vol = a.dv[0] * a.dv[1] * a.dv[2];
+                const double nV = a.vmom[cell * 20];
+                sscale = (T)(tot > 0.0 ? nV / (tot * vol) : 0.0);
+                atomicAdd(&a.counters[CNT_CLIPPED], 1ull);
+            }
+            __syncthreads();
+            scale = sscale;
         }
         T m[20];
 #pragma unroll

@@ -11,7 +11,10 @@
 // and reconstructed with the same CWENO polynomials as U. Fluxes are the
 // central-upwind (local Lax-Friedrichs) flux with the ten-moment wave speed
 // |u_d| + sqrt(3 Theta_dd) of the two neighbouring cells. One thread per cell
-// and stage; the step is O(N_x), negligible next to the phase-space passes.
+// and stage. The state stays in FP64; the reconstruction, fluxes and sources
+// (the right-hand side L) are computed in R = double in FP64 mode and in
+// R = float in FP32 mode (on GB300 the FP64 pipe runs at ~1/58 of the FP32
+// pipe), and the Runge-Kutta combination U0 + dt L is formed in FP64.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -31,24 +34,25 @@ __device__ __forceinline__ int s3(int a, int b, int c) {
     return y == 3 ? 6 : (y == 2 ? 7 : (y == 1 ? 8 : 9));
 }
 
-__device__ __forceinline__ void cweno3_point(double um, double u0, double up, double* left, double* right) {
-    const double eps = 1e-6;
-    double il = (u0 - um) * (u0 - um), ir = (up - u0) * (up - u0);
-    double d2 = up - 2.0 * u0 + um, d1 = up - um;
-    double ic = (13.0 / 3.0) * d2 * d2 + 0.25 * d1 * d1;
-    double al = 0.25 / ((eps + il) * (eps + il));
-    double ar = 0.25 / ((eps + ir) * (eps + ir));
-    double ac = 0.5 / ((eps + ic) * (eps + ic));
-    double sum = al + ar + ac;
-    double wl = al / sum, wr = ar / sum, wc = ac / sum;
+template <typename R>
+__device__ __forceinline__ void cweno3_point(R um, R u0, R up, R* left, R* right) {
+    const R eps = R(1e-6);
+    R il = (u0 - um) * (u0 - um), ir = (up - u0) * (up - u0);
+    R d2 = up - R(2) * u0 + um, d1 = up - um;
+    R ic = (R(13) / R(3)) * d2 * d2 + R(0.25) * d1 * d1;
+    R al = R(0.25) / ((eps + il) * (eps + il));
+    R ar = R(0.25) / ((eps + ir) * (eps + ir));
+    R ac = R(0.5) / ((eps + ic) * (eps + ic));
+    R inv = R(1) / (al + ar + ac);
+    R wl = al * inv, wr = ar * inv, wc = ac * inv;
     // values at xi = -1/2 and +1/2 of the linear left/right and the central
     // polynomial P_C = (P_opt - P_L/4 - P_R/4) / (1/2)
-    double base = u0 - d2 / 24.0 + 0.125 * d2;
-    double optl = base - 0.25 * d1, optr = base + 0.25 * d1;
-    double ll = u0 - 0.5 * (u0 - um), lr = u0 + 0.5 * (u0 - um);
-    double rl = u0 - 0.5 * (up - u0), rr = u0 + 0.5 * (up - u0);
-    double cl = 2.0 * optl - 0.5 * ll - 0.5 * rl;
-    double cr = 2.0 * optr - 0.5 * lr - 0.5 * rr;
+    R base = u0 - d2 / R(24) + R(0.125) * d2;
+    R optl = base - R(0.25) * d1, optr = base + R(0.25) * d1;
+    R ll = u0 - R(0.5) * (u0 - um), lr = u0 + R(0.5) * (u0 - um);
+    R rl = u0 - R(0.5) * (up - u0), rr = u0 + R(0.5) * (up - u0);
+    R cl = R(2) * optl - R(0.5) * ll - R(0.5) * rl;
+    R cr = R(2) * optr - R(0.5) * lr - R(0.5) * rr;
     *left = wl * ll + wr * rl + wc * cl;
     *right = wl * lr + wr * rr + wc * cr;
 }
@@ -56,6 +60,7 @@ __device__ __forceinline__ void cweno3_point(double um, double u0, double up, do
 struct FluidCtx {
     const FluidArgs* a;
     int nc, nq, qoff;
+    bool use0, use1;  // wq0 != 0, wq1 != 0 (decided once per thread)
 };
 
 // sign of a component under y -> -y (v_y -> -v_y)
@@ -86,34 +91,39 @@ __device__ __forceinline__ long long resolve(const FluidArgs& a, int ix, int iy,
     return (long long)iy * a.nx + ix;
 }
 
-__device__ __forceinline__ double state_at(const FluidCtx& c, int k, int ix, int iy) {
+template <typename R>
+__device__ __forceinline__ R state_at(const FluidCtx& c, int k, int ix, int iy) {
     bool mir;
     long long id = resolve(*c.a, ix, iy, &mir);
-    double v = c.a->Us[id * c.nc + k];
-    return (mir && c.a->nvdim == 3) ? v * parity_state(k) : v;
+    R v = (R)c.a->Us[id * c.nc + k];
+    return (mir && c.a->nvdim == 3) ? v * (R)parity_state(k) : v;
 }
 
-__device__ __forceinline__ double q_at(const FluidCtx& c, int k, int ix, int iy) {
+// Q = wq0 q0 + wq1 q1 (the weights are 0, 1/2 or 1, exact in R)
+template <typename R>
+__device__ __forceinline__ R q_at(const FluidCtx& c, int k, int ix, int iy) {
     bool mir;
     long long id = resolve(*c.a, ix, iy, &mir);
     const FluidArgs& a = *c.a;
-    double v = 0.0;
-    if (a.wq0 != 0.0) v += a.wq0 * a.q0[id * a.nmom + c.qoff + k];
-    if (a.wq1 != 0.0) v += a.wq1 * a.q1[id * a.nmom + c.qoff + k];
-    return (mir && a.nvdim == 3) ? v * parity_q(k) : v;
+    R v = R(0);
+    if (c.use0) v += (R)a.wq0 * (R)a.q0[id * a.nmom + c.qoff + k];
+    if (c.use1) v += (R)a.wq1 * (R)a.q1[id * a.nmom + c.qoff + k];
+    return (mir && a.nvdim == 3) ? v * (R)parity_q(k) : v;
 }
 
-__device__ __forceinline__ double wave_speed(int nvdim, int dir, const double* u) {
-    double n = u[0];
-    if (!(n > 0.0)) return 0.0;
-    double ud = u[1 + dir] / n;
-    double e2 = nvdim == 1 ? u[2] : u[4 + s2(dir, dir)];
-    double th = e2 / n - ud * ud;
-    if (th < 0.0) th = 0.0;
-    return fabs(ud) + sqrt(3.0 * th);
+template <typename R>
+__device__ __forceinline__ R wave_speed(int nvdim, int dir, const R* u) {
+    R n = u[0];
+    if (!(n > R(0))) return R(0);
+    R ud = u[1 + dir] / n;
+    R e2 = nvdim == 1 ? u[2] : u[4 + s2(dir, dir)];
+    R th = e2 / n - ud * ud;
+    if (th < R(0)) th = R(0);
+    return fabs(ud) + sqrt(R(3) * th);
 }
 
-__device__ __forceinline__ double flux_of(int nvdim, int dir, int k, const double* u, const double* q) {
+template <typename R>
+__device__ __forceinline__ R flux_of(int nvdim, int dir, int k, const R* u, const R* q) {
     if (nvdim == 1) return k == 0 ? u[1] : (k == 1 ? u[2] : q[0]);
     if (k == 0) return u[1 + dir];
     if (k < 4) return u[4 + s2(dir, k - 1)];
@@ -123,35 +133,38 @@ __device__ __forceinline__ double flux_of(int nvdim, int dir, int k, const doubl
 
 // numerical flux through the interface between cell (lx, ly) and its
 // neighbour in direction dir
-__device__ void interface_flux(const FluidCtx& c, int dir, int lx, int ly, double* H) {
+template <typename R>
+__device__ void interface_flux(const FluidCtx& c, int dir, int lx, int ly, R* H) {
     const int ox = dir == 0, oy = dir == 1;
-    double uL[10], uR[10], cL[10], cR[10], qL[10], qR[10];
+    R uL[10], uR[10], cL[10], cR[10], qL[10], qR[10];
     for (int k = 0; k < c.nc; ++k) {
-        double a0 = state_at(c, k, lx - ox, ly - oy), a1 = state_at(c, k, lx, ly);
-        double a2 = state_at(c, k, lx + ox, ly + oy), a3 = state_at(c, k, lx + 2 * ox, ly + 2 * oy);
-        double l, r;
-        cweno3_point(a0, a1, a2, &l, &r);
+        R a0 = state_at<R>(c, k, lx - ox, ly - oy), a1 = state_at<R>(c, k, lx, ly);
+        R a2 = state_at<R>(c, k, lx + ox, ly + oy), a3 = state_at<R>(c, k, lx + 2 * ox, ly + 2 * oy);
+        R l, r;
+        cweno3_point<R>(a0, a1, a2, &l, &r);
         uL[k] = r;
-        cweno3_point(a1, a2, a3, &l, &r);
+        cweno3_point<R>(a1, a2, a3, &l, &r);
         uR[k] = l;
         cL[k] = a1;
         cR[k] = a2;
     }
     for (int k = 0; k < c.nq; ++k) {
-        double a0 = q_at(c, k, lx - ox, ly - oy), a1 = q_at(c, k, lx, ly);
-        double a2 = q_at(c, k, lx + ox, ly + oy), a3 = q_at(c, k, lx + 2 * ox, ly + 2 * oy);
-        double l, r;
-        cweno3_point(a0, a1, a2, &l, &r);
+        R a0 = q_at<R>(c, k, lx - ox, ly - oy), a1 = q_at<R>(c, k, lx, ly);
+        R a2 = q_at<R>(c, k, lx + ox, ly + oy), a3 = q_at<R>(c, k, lx + 2 * ox, ly + 2 * oy);
+        R l, r;
+        cweno3_point<R>(a0, a1, a2, &l, &r);
         qL[k] = r;
-        cweno3_point(a1, a2, a3, &l, &r);
+        cweno3_point<R>(a1, a2, a3, &l, &r);
         qR[k] = l;
     }
     const int nvdim = c.a->nvdim;
-    double sp = fmax(wave_speed(nvdim, dir, cL), wave_speed(nvdim, dir, cR));
+    R sp = fmax(wave_speed<R>(nvdim, dir, cL), wave_speed<R>(nvdim, dir, cR));
     for (int k = 0; k < c.nc; ++k)
-        H[k] = 0.5 * (flux_of(nvdim, dir, k, uL, qL) + flux_of(nvdim, dir, k, uR, qR)) - 0.5 * sp * (uR[k] - uL[k]);
+        H[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, uL, qL) + flux_of<R>(nvdim, dir, k, uR, qR)) -
+               R(0.5) * sp * (uR[k] - uL[k]);
 }
 
+template <typename R>
 __global__ void fluid_stage_kernel(FluidArgs a) {
     long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (cell >= (long long)a.nx * a.ny) return;
@@ -161,35 +174,38 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
     c.nc = a.nvdim == 1 ? 3 : 10;
     c.nq = a.nvdim == 1 ? 1 : 10;
     c.qoff = a.nvdim == 1 ? 3 : 10;
-    double L[10];
-    for (int k = 0; k < c.nc; ++k) L[k] = 0.0;
+    c.use0 = a.wq0 != 0.0;
+    c.use1 = a.wq1 != 0.0;
+    R L[10];
+    for (int k = 0; k < c.nc; ++k) L[k] = R(0);
     const int ndir = a.nvdim == 1 ? 1 : 2;
-    double Hm[10], Hp[10];
+    R Hm[10], Hp[10];
     for (int dir = 0; dir < ndir; ++dir) {
-        const double h = dir == 0 ? a.dx : a.dy;
-        interface_flux(c, dir, ix - (dir == 0), iy - (dir == 1), Hm);
-        interface_flux(c, dir, ix, iy, Hp);
+        const R invh = (R)(1.0 / (dir == 0 ? a.dx : a.dy));
+        interface_flux<R>(c, dir, ix - (dir == 0), iy - (dir == 1), Hm);
+        interface_flux<R>(c, dir, ix, iy, Hp);
         // walls: the interface beyond the last row is the wall itself
         // (mirror ghosts already give its flux); nothing special needed
-        for (int k = 0; k < c.nc; ++k) L[k] -= (Hp[k] - Hm[k]) / h;
+        for (int k = 0; k < c.nc; ++k) L[k] -= (Hp[k] - Hm[k]) * invh;
     }
-    const double* u = a.Us + cell * c.nc;
-    const double* eb = a.eb + cell * 6;
-    const double qm = a.qm;
+    R u[10], eb[6];
+    for (int k = 0; k < c.nc; ++k) u[k] = (R)a.Us[cell * c.nc + k];
+    for (int k = 0; k < 6; ++k) eb[k] = (R)a.eb[cell * 6 + k];
+    const R qm = (R)a.qm;
     if (a.nvdim == 1) {
         L[1] += qm * u[0] * eb[0];
-        L[2] += qm * 2.0 * u[1] * eb[0];
+        L[2] += qm * R(2) * u[1] * eb[0];
     } else {
-        const double* E = eb;
-        const double* B = eb + 3;
-        const double* nu = u + 1;
+        const R* E = eb;
+        const R* B = eb + 3;
+        const R* nu = u + 1;
         L[1] += qm * (u[0] * E[0] + nu[1] * B[2] - nu[2] * B[1]);
         L[2] += qm * (u[0] * E[1] + nu[2] * B[0] - nu[0] * B[2]);
         L[3] += qm * (u[0] * E[2] + nu[0] * B[1] - nu[1] * B[0]);
-        double M[3][3];
+        R M[3][3];
         for (int p = 0; p < 3; ++p)
             for (int q = 0; q < 3; ++q) M[p][q] = u[4 + s2(p, q)];
-        double C[3][3];
+        R C[3][3];
         for (int p = 0; p < 3; ++p) {
             C[p][0] = M[p][1] * B[2] - M[p][2] * B[1];
             C[p][1] = M[p][2] * B[0] - M[p][0] * B[2];
@@ -201,14 +217,15 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
     for (int k = 0; k < c.nc; ++k) {
         double us = a.Us[cell * c.nc + k];
         double u0 = a.a0 != 0.0 ? a.U0[cell * c.nc + k] : 0.0;
-        a.Uout[cell * c.nc + k] = a.a0 * u0 + a.a1 * (us + a.dt * L[k]);
+        a.Uout[cell * c.nc + k] = a.a0 * u0 + a.a1 * (us + a.dt * (double)L[k]);
     }
 }
 
 cudaError_t launch_fluid_stage(const FluidArgs& a, cudaStream_t st) {
     long long n = (long long)a.nx * a.ny;
     int threads = 128;
-    fluid_stage_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+    if (a.precision == 64) fluid_stage_kernel<double><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+    else fluid_stage_kernel<float><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
     count_launch();
     return cudaGetLastError();
 }

@@ -108,6 +108,7 @@ struct FluidArgs {
     double wq0, wq1;        // Q = wq0 * q0 + wq1 * q1
     const double* eb;
     int nx, ny, bc_y, nvdim, nmom;
+    int precision;          // 64: right-hand side in FP64; 32: in FP32 (state FP64)
     double dx, dy, qm, dt;
     double a0, a1;          // Uout = a0 * U0 + a1 * (Us + dt L(Us))
 };

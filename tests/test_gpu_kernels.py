@@ -223,11 +223,19 @@ def test_moment_fit_matches_oracle(gpu, orc, precision):
     r.close()
 
 
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("bc_y", [1, 0])
-def test_fluid_step_matches_oracle(gpu, orc, bc_y):
+def test_fluid_step_matches_oracle(gpu, orc, bc_y, precision):
+    """FP64 mode: same arithmetic up to rounding order -> 1e-11. FP32 mode:
+    the right-hand side is evaluated in FP32 (state and the Runge-Kutta
+    combination in FP64): rounding of the inputs and of the flux differences
+    (relative ~1e-7 of |H|) enters multiplied by dt/h times the wave speed
+    over three stages, and the CWENO weights amplify it a little (observed
+    ~2e-6 of each component's scale); the bound is the FP32-mode moment
+    tolerance, 1e-5 of each component's scale."""
     from gpu_util import AbiRunner
     from paper_2109_06743_gb300 import abi
-    cfg = small_harris(nx=10, ny=8, nv=8, precision=64, bc_y=bc_y)
+    cfg = small_harris(nx=10, ny=8, nv=8, precision=precision, bc_y=bc_y)
     f0 = near_maxwellian_state(cfg, 500)
     g = oracle_grid(orc, cfg)
     U0 = fluid_targets(cfg, orc, f0, 501)
@@ -251,7 +259,12 @@ def test_fluid_step_matches_oracle(gpu, orc, bc_y):
         q0 = mt[k].cpu().numpy()[:, 10:20].copy()
         q1 = mt1[k].cpu().numpy()[:, 10:20].copy()
         orc.fluid_step(Uref, g, oracle_species(orc, sp), q0, 0.5 * (q0 + q1), q1, eb, dt)
-        np.testing.assert_allclose(r.fluid[k].cpu().numpy(), Uref, rtol=1e-11, atol=1e-13 * np.abs(Uref).max())
+        got = r.fluid[k].cpu().numpy()
+        if precision == 64:
+            np.testing.assert_allclose(got, Uref, rtol=1e-11, atol=1e-13 * np.abs(Uref).max())
+        else:
+            scale = np.abs(Uref).max(axis=0, keepdims=True)
+            assert np.all(np.abs(got - Uref) <= 1e-5 * scale), float((np.abs(got - Uref) / scale).max())
     r.close()
 
 
