@@ -145,8 +145,9 @@ vl_status moments(vl_ctx* ctx, int species, double* mom_out, vl_stream_t stream)
  * V and the rescaled F targets); then f <- f - f_M,V + f_M,F, negative values
  * are clipped and the cell rescaled to n_V (limiter of Algorithm 1). The
  * fluid state is replaced by its rescaled moments. use_mlp != 0 starts Newton
- * from the trained network (mlp_set_weights) instead of the continuous
- * Maxwellian. If theta_v/theta_f are not NULL the fitted parameters are
+ * from the network's prediction (see the MLP section below; needs weights
+ * from mlp_init/mlp_train or mlp_set_weights) instead of the continuous
+ * Maxwellian, with the cold start as the fallback. If theta_v/theta_f are not NULL the fitted parameters are
  * written there. If mom_out is not NULL the raw moments of the new f are
  * written there. In place on f and the fluid state. */
 vl_status moment_fit(vl_ctx* ctx, int species, const double* vmom, int use_mlp,
@@ -179,6 +180,56 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t,
  * Paper Sec. 2.1 (FDTD, two half steps per time step) and Sec. 3.1. */
 vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom,
                        vl_stream_t stream);
+
+/* ---- MLP warm start of the moment fit (Sec. 2.2; the learned part) --------
+ * A 12 -> 128 -> 128 -> 10 GELU network predicts, per fit, the Newton
+ * solution minus the cold start (eta* - eta_0 in the fit's scaled
+ * coordinates) from 12 inputs of the fit targets: Theta_ab/(dv_a dv_b) (6),
+ * (u_a - nearest cell centre)/dv_a (3), (u_a - vmin_a)/(vmax_a - vmin_a) (3).
+ * moment_fit_solve(use_mlp = 1) starts Newton there; Newton still runs to
+ * fit_tol and restarts from the cold start if the warm run fails, so the
+ * fitted Maxwellians do not depend on the network. All GEMMs (inference and
+ * training) run on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation). The parameters live in the context's workspace as FP32:
+ *   xm[12] xs[12] ym[10] ys[10] ysc[10] | W1[128][12] b1[128] | W2[128][128]
+ *   b2[128] | W3[10][128] b3[10]  (W[out][in]; inputs standardised by xm,
+ *   xs; the network's outputs are y = asinh(t / ysc) standardised by ym, ys).
+ *   Training samples: VL_MLP_SAMPLE floats each, x[12], t[10]
+ *   (= eta* - eta_0), flag (1 = usable), pad. */
+#define VL_MLP_NPARAM 19520
+#define VL_MLP_SAMPLE 24
+
+/* Random (Glorot-uniform, seeded) weights, zero biases, unit normalisation,
+ * cleared Adam state. Synchronous. */
+vl_status mlp_init(vl_ctx* ctx, unsigned long long seed);
+/* Copy VL_MLP_NPARAM floats from / to host memory. Synchronous. */
+vl_status mlp_set_weights(vl_ctx* ctx, const float* w_host);
+vl_status mlp_get_weights(vl_ctx* ctx, float* w_host);
+/* From the next moment_fit_solve on, every converged 2D3V fit appends one
+ * training sample to samples_dev (device, capacity samples; later fits are
+ * dropped); capacity 0 stops harvesting. Resets the count. */
+vl_status mlp_set_harvest(vl_ctx* ctx, float* samples_dev, long long capacity, vl_stream_t stream);
+/* Number of samples harvested so far (at most the capacity). Synchronises. */
+vl_status mlp_harvest_count(vl_ctx* ctx, long long* n, vl_stream_t stream);
+/* Normalisation constants from n samples: input means and deviations;
+ * output scales ysc = geometric means of |t| (at least 1e-6), then the means
+ * ym of asinh(t / ysc) and ys = max(1, their deviations). */
+vl_status mlp_normalize(vl_ctx* ctx, const float* samples_dev, long long n, vl_stream_t stream);
+/* `steps` Adam steps (lr, beta 0.9 / 0.999) on the mean-square error of the
+ * standardised transformed outputs, each on `batch` samples (a multiple of 128) drawn
+ * from the n samples by a counter hash of seed and the step. loss_host (or
+ * NULL) receives the loss of every step (synchronises per step). */
+vl_status mlp_train(vl_ctx* ctx, const float* samples_dev, long long n, int steps, int batch,
+                    float lr, unsigned long long seed, double* loss_host, vl_stream_t stream);
+/* The network on raw inputs x_dev[n][12] -> y_dev[n][10] (eta* - eta_0);
+ * NaN rows of inputs give NaN outputs. Synchronises. */
+vl_status mlp_forward(vl_ctx* ctx, const float* x_dev, long long n, float* y_dev, vl_stream_t stream);
+/* Gradient of the training loss (mean over the n samples and 10 outputs of
+ * the squared error of the standardised transformed outputs) with respect to all VL_MLP_NPARAM
+ * parameters (zero for the normalisation constants) into grad_dev, and the
+ * loss into *loss_host (or NULL). Synchronises. */
+vl_status mlp_grad(vl_ctx* ctx, const float* samples_dev, long long n, float* grad_dev,
+                   double* loss_host, vl_stream_t stream);
 
 /* Device counters accumulated since the last reset: out[0] Newton
  * iterations, out[1] Newton fallbacks, out[2] clipped cells, out[3] cells

@@ -19,7 +19,11 @@ VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
             "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
-            "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count"]
+            "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
+            "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
+            "mlp_grad"]
+MLP_NPARAM = 19520  # VL_MLP_NPARAM
+MLP_SAMPLE = 24     # VL_MLP_SAMPLE
 
 
 class VlasovError(RuntimeError):
@@ -85,6 +89,17 @@ def lib():
     L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.vl_reset_stats.argtypes = [_vp, _vp]
+    F = ctypes.POINTER(ctypes.c_float)
+    L.mlp_init.argtypes = [_vp, ctypes.c_ulonglong]
+    L.mlp_set_weights.argtypes = [_vp, F]
+    L.mlp_get_weights.argtypes = [_vp, F]
+    L.mlp_set_harvest.argtypes = [_vp, _vp, ctypes.c_longlong, _vp]
+    L.mlp_harvest_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
+    L.mlp_normalize.argtypes = [_vp, _vp, ctypes.c_longlong, _vp]
+    L.mlp_train.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                            ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double), _vp]
+    L.mlp_forward.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp]
+    L.mlp_grad.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, ctypes.POINTER(ctypes.c_double), _vp]
     L.vl_launch_count.argtypes = []
     L.vl_launch_count.restype = ctypes.c_longlong
     for name in EXPORTED:
@@ -219,3 +234,56 @@ def vl_reset_stats(ctx, stream=None):
 
 def vl_launch_count():
     return int(lib().vl_launch_count())
+
+
+# ---- MLP warm start ------------------------------------------------------------------
+
+def mlp_init(ctx, seed=0):
+    _check(ctx, lib().mlp_init(ctx, int(seed)))
+
+
+def mlp_set_weights(ctx, w):
+    """w: numpy float32 array of MLP_NPARAM values (host)."""
+    import numpy as np
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == MLP_NPARAM
+    _check(ctx, lib().mlp_set_weights(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+
+def mlp_get_weights(ctx):
+    import numpy as np
+    w = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(ctx, lib().mlp_get_weights(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return w
+
+
+def mlp_set_harvest(ctx, samples, capacity, stream=None):
+    _check(ctx, lib().mlp_set_harvest(ctx, ptr(samples), int(capacity), stream_handle(stream)))
+
+
+def mlp_harvest_count(ctx, stream=None):
+    n = ctypes.c_longlong(0)
+    _check(ctx, lib().mlp_harvest_count(ctx, ctypes.byref(n), stream_handle(stream)))
+    return n.value
+
+
+def mlp_normalize(ctx, samples, n, stream=None):
+    _check(ctx, lib().mlp_normalize(ctx, ptr(samples), int(n), stream_handle(stream)))
+
+
+def mlp_train(ctx, samples, n, steps, batch=4096, lr=1e-3, seed=0, record_loss=False, stream=None):
+    """Returns the per-step losses if record_loss, else None."""
+    loss = (ctypes.c_double * max(1, steps))() if record_loss else None
+    _check(ctx, lib().mlp_train(ctx, ptr(samples), int(n), int(steps), int(batch), float(lr), int(seed),
+                                loss, stream_handle(stream)))
+    return list(loss)[:steps] if record_loss else None
+
+
+def mlp_forward(ctx, x, n, y, stream=None):
+    _check(ctx, lib().mlp_forward(ctx, ptr(x), int(n), ptr(y), stream_handle(stream)))
+
+
+def mlp_grad(ctx, samples, n, grad, stream=None):
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib().mlp_grad(ctx, ptr(samples), int(n), ptr(grad), ctypes.byref(loss), stream_handle(stream)))
+    return loss.value

@@ -6,9 +6,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "mlp_common.cuh"
 
 struct vl_ctx {
     vl_desc d;
@@ -18,8 +20,25 @@ struct vl_ctx {
     double* eb;
     vl::Workspace ws;
     vl::MomConv conv[VL_MAX_SPECIES];
+    // MLP warm start (workspace sections)
+    float* mlp_w;           // [NPARAM] FP32 parameters
+    float* mlp_m;           // Adam first moments
+    float* mlp_v;           // Adam second moments
+    float* mlp_g;           // gradient accumulator
+    double* mlp_acc;        // [45] sample statistics, then [1] loss
+    double* mlp_loss;
+    int* mlp_err;
+    float* mlp_pred;        // [ncell][2][10] predictions of the current species
+    unsigned long long* harvest_count;
+    bool mlp_ready;
+    int adam_step;
+    float* harvest;
+    long long harvest_cap;
     char err[512];
 };
+
+static_assert(VL_MLP_NPARAM == vl::mlp::kNParam, "parameter blob size");
+static_assert(VL_MLP_SAMPLE == vl::mlp::kSample, "sample size");
 
 namespace vl {
 static std::atomic<long long> g_launches{0};
@@ -53,7 +72,8 @@ long long vblock_of(const vl_desc& d, int s) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, counters, total;
+    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, counters;
+    size_t mlp_w, mlp_m, mlp_v, mlp_g, mlp_acc, mlp_err, mlp_pred, harvest_count, total;
 };
 
 Layout layout_of(const vl_desc& d) {
@@ -68,6 +88,15 @@ Layout layout_of(const vl_desc& d) {
     L.u2 = off; off = align256(off + nc * 10 * sizeof(double));
     L.cur = off; off = align256(off + nc * 3 * sizeof(double));
     L.counters = off; off = align256(off + VL_NSTATS * sizeof(unsigned long long));
+    const size_t np = (size_t)VL_MLP_NPARAM * sizeof(float);
+    L.mlp_w = off; off = align256(off + np);
+    L.mlp_m = off; off = align256(off + np);
+    L.mlp_v = off; off = align256(off + np);
+    L.mlp_g = off; off = align256(off + np);
+    L.mlp_acc = off; off = align256(off + 56 * sizeof(double));
+    L.mlp_err = off; off = align256(off + sizeof(int));
+    L.mlp_pred = off; off = align256(off + nc * 20 * sizeof(float));
+    L.harvest_count = off; off = align256(off + sizeof(unsigned long long));
     L.total = off;
     return L;
 }
@@ -173,6 +202,19 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     c->ws.cur = reinterpret_cast<double*>(w + L.cur);
     c->ws.counters = reinterpret_cast<unsigned long long*>(w + L.counters);
     c->ws.mlp = nullptr;
+    c->mlp_w = reinterpret_cast<float*>(w + L.mlp_w);
+    c->mlp_m = reinterpret_cast<float*>(w + L.mlp_m);
+    c->mlp_v = reinterpret_cast<float*>(w + L.mlp_v);
+    c->mlp_g = reinterpret_cast<float*>(w + L.mlp_g);
+    c->mlp_acc = reinterpret_cast<double*>(w + L.mlp_acc);
+    c->mlp_loss = c->mlp_acc + 55;
+    c->mlp_err = reinterpret_cast<int*>(w + L.mlp_err);
+    c->mlp_pred = reinterpret_cast<float*>(w + L.mlp_pred);
+    c->harvest_count = reinterpret_cast<unsigned long long*>(w + L.harvest_count);
+    c->mlp_ready = false;
+    c->adam_step = 0;
+    c->harvest = nullptr;
+    c->harvest_cap = 0;
     for (int s = 0; s < desc->nspecies; ++s) {
         double vmin[3], dv[3];
         fill_box(*desc, s, vmin, dv);
@@ -339,8 +381,9 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
-    if (use_mlp) return fail(ctx, VL_EINVAL, "no MLP weights have been set on this context");
     const vl_desc& d = ctx->d;
+    if (use_mlp && !ctx->mlp_ready) return fail(ctx, VL_EINVAL, "use_mlp: no MLP weights on this context");
+    if (use_mlp && d.nvdim != 3) return fail(ctx, VL_ENOTSUP, "the MLP warm start serves the 2D3V fit");
     const int ncomp = d.nvdim == 1 ? 3 : 10;
     vl::FitArgs a;
     a.vmom = vmom;
@@ -349,13 +392,37 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     a.coef_f = ctx->ws.coef_f;
     a.status = ctx->ws.fit_status;
     a.counters = ctx->ws.counters;
-    a.mlp_w = nullptr;
+    a.warm = nullptr;
+    a.harvest = d.nvdim == 3 ? ctx->harvest : nullptr;
+    a.harvest_cap = ctx->harvest_cap;
+    a.harvest_count = ctx->harvest_count;
     a.ncell = ncell_of(d);
     a.nv = d.nv[s][0];
     fill_box(d, s, a.vmin, a.dv);
+    for (int q = 0; q < 3; ++q) a.vmax[q] = a.vmin[q] + a.dv[q] * (d.nvdim == 3 || q == 0 ? d.nv[s][q] : 1);
     a.tol = d.fit_tol;
     a.max_iter = d.fit_max_iter;
     cudaStream_t cs = (cudaStream_t)stream;
+    if (use_mlp) {
+        vl::MlpInferArgs m;
+        m.w = ctx->mlp_w;
+        m.mode = 0;
+        m.vmom = vmom;
+        m.fluid = a.fluid;
+        m.nmom = 20;
+        m.x = nullptr;
+        m.nfit = 2 * a.ncell;
+        for (int q = 0; q < 3; ++q) {
+            m.vmin[q] = a.vmin[q];
+            m.dv[q] = a.dv[q];
+            m.vmax[q] = a.vmax[q];
+        }
+        m.y = ctx->mlp_pred;
+        m.err = ctx->mlp_err;
+        st = cuda_check(ctx, vl::launch_mlp_infer(m, cs), "moment_fit (MLP warm start)");
+        if (st != VL_OK) return st;
+        a.warm = ctx->mlp_pred;
+    }
     st = cuda_check(ctx, vl::launch_fit(a, d.nvdim, cs), "moment_fit (Newton)");
     if (st != VL_OK) return st;
     if (theta_v) {
@@ -472,6 +539,185 @@ vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_strea
     a.c2 = d.c * d.c;
     a.h = h;
     return cuda_check(ctx, vl::launch_maxwell(a, cs), "maxwell_step (FDTD)");
+}
+
+// ---------------------------------------------------------------- MLP warm start
+
+namespace {
+unsigned long long splitmix64(unsigned long long& s) {
+    unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+vl_status mlp_check_err(vl_ctx* ctx, cudaStream_t cs, const char* what) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->mlp_err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    if (h) return fail(ctx, VL_ECUDA, "%s: a tensor-core wait timed out", what);
+    return VL_OK;
+}
+}  // namespace
+
+vl_status mlp_init(vl_ctx* ctx, unsigned long long seed) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    std::vector<float> w(VL_MLP_NPARAM, 0.f);
+    // unit normalisation until mlp_normalize sets it from samples
+    for (int q = 0; q < 12; ++q) w[vl::mlp::kOffXs + q] = 1.f;
+    for (int q = 0; q < 10; ++q) w[vl::mlp::kOffYs + q] = 1.f;
+    for (int q = 0; q < 10; ++q) w[vl::mlp::kOffYsc + q] = 1.f;
+    unsigned long long st = seed;
+    auto uniform = [&]() { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); };
+    // Glorot-uniform weights, zero biases
+    const int fan[3][2] = {{12, 128}, {128, 128}, {128, 10}};
+    const int off[3] = {vl::mlp::kOffW1, vl::mlp::kOffW2, vl::mlp::kOffW3};
+    for (int l = 0; l < 3; ++l) {
+        const double lim = std::sqrt(6.0 / (fan[l][0] + fan[l][1]));
+        for (int q = 0; q < fan[l][0] * fan[l][1]; ++q) w[off[l] + q] = (float)((2.0 * uniform() - 1.0) * lim);
+    }
+    cudaError_t e = cudaMemcpy(ctx->mlp_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_m, 0, VL_MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_v, 0, VL_MLP_NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_init");
+    ctx->adam_step = 0;
+    ctx->mlp_ready = true;
+    return VL_OK;
+}
+
+vl_status mlp_set_weights(vl_ctx* ctx, const float* w_host) {
+    if (!ctx || !w_host) return fail(ctx, VL_EINVAL, "NULL argument");
+    cudaError_t e = cudaMemcpy(ctx->mlp_w, w_host, VL_MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->mlp_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_set_weights");
+    ctx->mlp_ready = true;
+    return VL_OK;
+}
+
+vl_status mlp_get_weights(vl_ctx* ctx, float* w_host) {
+    if (!ctx || !w_host) return fail(ctx, VL_EINVAL, "NULL argument");
+    if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "no MLP weights on this context");
+    return cuda_check(ctx, cudaMemcpy(w_host, ctx->mlp_w, VL_MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost),
+                      "mlp_get_weights");
+}
+
+vl_status mlp_set_harvest(vl_ctx* ctx, float* samples_dev, long long capacity, vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    if (capacity < 0 || (capacity > 0 && !samples_dev)) return fail(ctx, VL_EINVAL, "bad harvest buffer");
+    ctx->harvest = capacity > 0 ? samples_dev : nullptr;
+    ctx->harvest_cap = capacity;
+    return cuda_check(ctx, cudaMemsetAsync(ctx->harvest_count, 0, sizeof(unsigned long long), (cudaStream_t)stream),
+                      "mlp_set_harvest");
+}
+
+vl_status mlp_harvest_count(vl_ctx* ctx, long long* n, vl_stream_t stream) {
+    if (!ctx || !n) return fail(ctx, VL_EINVAL, "NULL argument");
+    unsigned long long h = 0;
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->harvest_count, sizeof(h), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_harvest_count");
+    *n = (long long)(h < (unsigned long long)ctx->harvest_cap ? h : (unsigned long long)ctx->harvest_cap);
+    return VL_OK;
+}
+
+vl_status mlp_normalize(vl_ctx* ctx, const float* samples_dev, long long n, vl_stream_t stream) {
+    if (!ctx || !samples_dev || n <= 0) return fail(ctx, VL_EINVAL, "bad samples");
+    if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "call mlp_init first");
+    return cuda_check(ctx, vl::launch_mlp_stats(samples_dev, n, ctx->mlp_acc, ctx->mlp_w, (cudaStream_t)stream),
+                      "mlp_normalize");
+}
+
+vl_status mlp_train(vl_ctx* ctx, const float* samples_dev, long long n, int steps, int batch, float lr,
+                    unsigned long long seed, double* loss_host, vl_stream_t stream) {
+    if (!ctx || !samples_dev || n <= 0) return fail(ctx, VL_EINVAL, "bad samples");
+    if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "call mlp_init first");
+    if (steps < 0 || batch < 128 || batch % 128 != 0 || batch > (1 << 24) || !(lr > 0.f))
+        return fail(ctx, VL_EINVAL, "steps >= 0, batch a positive multiple of 128 and lr > 0 are required");
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (int k = 0; k < steps; ++k) {
+        cudaError_t e = cudaMemsetAsync(ctx->mlp_g, 0, VL_MLP_NPARAM * sizeof(float), cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(double), cs);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_train");
+        vl::MlpTrainArgs a;
+        a.w = ctx->mlp_w;
+        a.grad = ctx->mlp_g;
+        a.loss = ctx->mlp_loss;
+        a.samples = samples_dev;
+        a.n = n;
+        a.mode = 0;
+        a.rows = batch;
+        a.row0 = 0;
+        unsigned long long sk = seed ^ (0xD1B54A32D192ED03ull * (unsigned long long)(ctx->adam_step + 1));
+        a.seed = splitmix64(sk);
+        a.inv_count = 1.f / (float)(batch * 10);
+        a.err = ctx->mlp_err;
+        vl_status st = cuda_check(ctx, vl::launch_mlp_train_step(a, cs), "mlp_train (step)");
+        if (st != VL_OK) return st;
+        ctx->adam_step += 1;
+        st = cuda_check(ctx, vl::launch_mlp_adam(ctx->mlp_w, ctx->mlp_m, ctx->mlp_v, ctx->mlp_g, lr, ctx->adam_step, cs),
+                        "mlp_train (Adam)");
+        if (st != VL_OK) return st;
+        if (loss_host) {
+            double l = 0.0;
+            e = cudaMemcpyAsync(&l, ctx->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_train (loss)");
+            loss_host[k] = l / (double)(batch * 10);
+        }
+    }
+    return mlp_check_err(ctx, cs, "mlp_train");
+}
+
+vl_status mlp_forward(vl_ctx* ctx, const float* x_dev, long long n, float* y_dev, vl_stream_t stream) {
+    if (!ctx || n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(ctx, VL_EINVAL, "bad arguments");
+    if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "no MLP weights on this context");
+    vl::MlpInferArgs m = {};
+    m.w = ctx->mlp_w;
+    m.mode = 1;
+    m.x = x_dev;
+    m.nfit = n;
+    m.y = y_dev;
+    m.err = ctx->mlp_err;
+    cudaStream_t cs = (cudaStream_t)stream;
+    vl_status st = cuda_check(ctx, vl::launch_mlp_infer(m, cs), "mlp_forward");
+    if (st != VL_OK) return st;
+    return mlp_check_err(ctx, cs, "mlp_forward");
+}
+
+vl_status mlp_grad(vl_ctx* ctx, const float* samples_dev, long long n, float* grad_dev, double* loss_host,
+                   vl_stream_t stream) {
+    if (!ctx || !samples_dev || n <= 0 || !grad_dev) return fail(ctx, VL_EINVAL, "bad arguments");
+    if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "no MLP weights on this context");
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(grad_dev, 0, VL_MLP_NPARAM * sizeof(float), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(double), cs);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_grad");
+    for (long long r0 = 0; r0 < n; r0 += 128 * 1024) {
+        vl::MlpTrainArgs a;
+        a.w = ctx->mlp_w;
+        a.grad = grad_dev;
+        a.loss = ctx->mlp_loss;
+        a.samples = samples_dev;
+        a.n = n;
+        a.mode = 1;
+        a.row0 = r0;
+        a.rows = n - r0 < 128 * 1024 ? n - r0 : 128 * 1024;
+        a.seed = 0;
+        a.inv_count = 1.f / (float)(n * 10);
+        a.err = ctx->mlp_err;
+        vl_status st = cuda_check(ctx, vl::launch_mlp_train_step(a, cs), "mlp_grad");
+        if (st != VL_OK) return st;
+    }
+    if (loss_host) {
+        double l = 0.0;
+        e = cudaMemcpyAsync(&l, ctx->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "mlp_grad (loss)");
+        *loss_host = l / (double)(n * 10);
+    }
+    return mlp_check_err(ctx, cs, "mlp_grad");
 }
 
 vl_status vl_read_stats(vl_ctx* ctx, long long out[VL_NSTATS], vl_stream_t stream) {

@@ -69,14 +69,47 @@ struct FitArgs {
     double* coef_f;         // [ncell][16] of f_M,F
     int* status;            // [ncell][2]
     unsigned long long* counters;
-    const float* mlp_w;     // MLP weights or null
+    const float* warm;      // [ncell][2][10] predicted eta* - eta_0 (MLP), or null: cold start
+    float* harvest;         // training samples of converged fits, or null
+    long long harvest_cap;
+    unsigned long long* harvest_count;
     long long ncell;
     int nv;
-    double vmin[3], dv[3];
+    double vmin[3], dv[3], vmax[3];
     double tol;
     int max_iter;
 };
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
+
+// ---- MLP warm start (mlp.cu) ------------------------------------------------------
+struct MlpInferArgs {
+    const float* w;         // parameter blob (FP32)
+    int mode;               // 0: inputs from fit targets; 1: raw inputs x
+    const double* vmom;     // mode 0: [ncell][nmom] moments of f
+    const double* fluid;    // mode 0: [ncell][10] fluid state (not modified)
+    int nmom;
+    const float* x;         // mode 1: [nfit][12]
+    long long nfit;         // mode 0: 2 * ncell (fit 2c: V, 2c + 1: F)
+    double vmin[3], dv[3], vmax[3];
+    float* y;               // [nfit][10] eta* - eta_0 (NaN: no usable input)
+    int* err;               // set to 1 if a tensor-core wait timed out
+};
+struct MlpTrainArgs {
+    const float* w;
+    float* grad;            // [NPARAM] accumulated
+    double* loss;           // accumulated sum of squares
+    const float* samples;
+    long long n;
+    int mode;               // 0: rows drawn by a counter hash of (seed, row); 1: rows row0 + r
+    long long rows, row0;
+    unsigned long long seed;
+    float inv_count;        // 1 / (rows * 10)
+    int* err;
+};
+cudaError_t launch_mlp_stats(const float* samples, long long n, double* acc, float* w, cudaStream_t st);
+cudaError_t launch_mlp_infer(const MlpInferArgs& a, cudaStream_t st);
+cudaError_t launch_mlp_train_step(const MlpTrainArgs& a, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* w, float* m, float* v, const float* g, float lr, int step, cudaStream_t st);
 cudaError_t launch_newton3d(const FitArgs& a, cudaStream_t st);
 cudaError_t launch_theta(const double* coef, const int* status, int which, double* theta, long long ncell, int nvdim,
                          cudaStream_t st);
