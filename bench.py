@@ -8,6 +8,12 @@ both species. Inputs are synthetic (seeded Harris sheet, paper Sec. 3.3
 structure) and resident in HBM when the timed region starts; f (4.3 GB at
 the default size) is far larger than the 129 MB L2, so no flush is needed.
 
+The headline form is the paper's solver in FP32 with the Newton fits
+started from the warm-start network (FP32+MLP): the network is trained on
+the GPU during set-up, outside the timed region, on the converged fits of a
+cold-started 128 x 64 run with the same velocity grid; the line also reports
+the same steps with cold-started fits and the plain FP64 form.
+
 Metric: phase-space cell updates per second = (sum over species of
 spatial cells x velocity cells) x steps / time, over all ranks.
 
@@ -42,7 +48,12 @@ WORKLOADS = {
     # name: (nx, ny, nv, lx, ly)  -- Harris sheet, both species
     "harris_512x256_v16": (512, 256, 16, 25.6, 12.8),
     "harris_128x64_v20": (128, 64, 20, 25.6, 12.8),
+    "harris_128x64_v16": (128, 64, 16, 25.6, 12.8),
 }
+# warm-start network: trained on the fits of a smaller run with the same
+# velocity grid (the network's inputs are in units of the velocity cells)
+TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_128x64_v20": "harris_128x64_v20",
+              "harris_128x64_v16": "harris_128x64_v16"}
 
 
 def make_cfg(name, precision=32):
@@ -156,6 +167,42 @@ def newton_roofline(cfg, stats, fit_ms, launches):
             "evaluations": {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7]}}
 
 
+def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=4096, lr=2e-3):
+    """Harvest (inputs, eta* - eta_0) samples from the converged fits of a
+    cold-started run, train the network on the GPU, return its weights."""
+    import numpy as np
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300 import workloads as W
+    from paper_2109_06743_gb300.driver import Simulation
+    t0 = time.perf_counter()
+    cfg = make_cfg(name, precision=32)
+    sim = Simulation(cfg, W.harris_state(cfg, dtype=np.float32), None, W.harris_yee(cfg), device=device)
+    cap = harvest_steps * 4 * cfg.ncell
+    buf = torch.zeros((cap, abi.MLP_SAMPLE), dtype=torch.float32, device=device)
+    abi.mlp_set_harvest(sim.ctx, buf, cap, sim.stream)
+    for _ in range(harvest_steps):
+        sim.step()
+    n = abi.mlp_harvest_count(sim.ctx, sim.stream)
+    abi.mlp_set_harvest(sim.ctx, None, 0, sim.stream)
+    abi.mlp_init(sim.ctx, 2109)
+    abi.mlp_normalize(sim.ctx, buf, n, sim.stream)
+    t1 = time.perf_counter()
+    losses = abi.mlp_train(sim.ctx, buf, n, train_steps, batch=batch, lr=lr, seed=6743, record_loss=True,
+                           stream=sim.stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    w = abi.mlp_get_weights(sim.ctx)
+    sim.close()
+    del buf
+    info = {"trained_on": "%s, %d cold-started steps" % (name, harvest_steps), "samples": int(n),
+            "train_steps": train_steps, "batch": batch, "lr": lr,
+            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+            "harvest_seconds": t1 - t0, "train_seconds": t2 - t1}
+    return w, info
+
+
 def cpu_baseline(steps=1, sample=(32, 16)):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     a 32x16 spatial subdomain with the workload's dx, dv (both species),
@@ -208,6 +255,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form timed for comparison")
+    ap.add_argument("--no-mlp", action="store_true", help="cold-started fits only (no warm-start network)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -235,9 +283,14 @@ def main():
         dist.barrier()
     abi.lib()
 
+    device = "cuda:%d" % local
+    mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(TRAIN_FROM[args.workload], device)
+    use_mlp = mlp_w is not None
     cfg = make_cfg(args.workload, precision=32)
     f0 = W.harris_state(cfg, dtype=np.float32)
-    sim = Simulation(cfg, f0, None, W.harris_yee(cfg), device="cuda:%d" % local)
+    sim = Simulation(cfg, f0, None, W.harris_yee(cfg), device=device)
+    if use_mlp:
+        abi.mlp_set_weights(sim.ctx, mlp_w)
     stream = sim.stream
     cells = cfg.phase_cells()
 
@@ -248,7 +301,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        sim.step()
+        sim.step(use_mlp=use_mlp)
     abi.vl_reset_stats(sim.ctx, stream)
     barrier_sync()
 
@@ -271,7 +324,7 @@ def main():
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(args.steps):
-        sim.step(mark=mark)
+        sim.step(use_mlp=use_mlp, mark=mark)
     t_end.record(stream)
     barrier_sync()
     launches = abi.vl_launch_count() - launches0
@@ -307,6 +360,25 @@ def main():
     else:
         roof = newton
 
+    # ---- the same steps with the cold-started fit (no network) ----------------
+    cold = None
+    if use_mlp:
+        kc = max(1, min(args.steps, 5))
+        abi.vl_reset_stats(sim.ctx, stream)
+        barrier_sync()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(kc):
+            sim.step(use_mlp=False)
+        c1.record(stream)
+        barrier_sync()
+        tc_ = c0.elapsed_time(c1) / 1e3
+        cst = abi.vl_read_stats(sim.ctx, stream)
+        nfit = 2 * cfg.ncell * len(cfg.species)
+        cold = {"value": cells * kc / tc_, "unit": UNIT, "ms_per_step": 1e3 * tc_ / kc, "steps": kc,
+                "newton_iterations_per_fit": cst[0] / (nfit * kc), "newton_fallbacks_per_fit": cst[1] / (nfit * kc)}
+
     # ---- end to end through the public API with host buffers ------------------
     e2e = None
     if not args.no_e2e:
@@ -322,7 +394,7 @@ def main():
             for _ in range(ksteps):
                 for h, f in zip(host, sim.f):
                     f.copy_(h, non_blocking=True)
-                sim.step()
+                sim.step(use_mlp=use_mlp)
                 for h, f in zip(host, sim.f):
                     h.copy_(f, non_blocking=True)
         e1.record(stream)
@@ -336,7 +408,13 @@ def main():
         e2e = {"value": cells * ksteps * world / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ksteps}
 
-    fit_iters = stats[0] / max(1, 2 * cfg.ncell * len(cfg.species) * args.steps)
+    nfits = max(1, 2 * cfg.ncell * len(cfg.species) * args.steps)
+    fit_iters = stats[0] / nfits
+    if use_mlp:
+        mlp_info.update({"newton_iterations_per_fit": fit_iters, "newton_fallbacks_per_fit": stats[1] / nfits,
+                         "cold_start": cold,
+                         "applied_to": args.workload + " (same 16^3-per-species velocity grid)"
+                         if TRAIN_FROM[args.workload] != args.workload else args.workload})
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -347,7 +425,8 @@ def main():
         cfg64 = make_cfg(args.workload, precision=64)
         s64 = Simulation(cfg64, W.harris_state(cfg64, dtype=np.float64), None, W.harris_yee(cfg64),
                          device="cuda:%d" % local)
-        s64.step()
+        for _ in range(3):
+            s64.step()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -370,7 +449,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [cfg.nx, cfg.ny], "nv": cfg.species[0].nv[0],
                    "species": len(cfg.species), "phase_cells_per_gpu": cells,
-                   "precision": "f32 f and sweeps; f64 moments, Newton fit, fluid, fields",
+                   "precision": "f32 f, sweeps and fluid right-hand side; f64 moment sums, fluid state, fields; "
+                                "double-float Newton fit" + ("; BF16 warm-start network" if use_mlp else ""),
                    "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
                        sum(cfg.ncell * s.vblock for s in cfg.species) * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -378,6 +458,7 @@ def main():
         "phases_ms_per_step": {k: v / args.steps for k, v in sorted(phase_ms.items())},
         "hbm_phases": rows,
         "newton_iterations_per_fit": fit_iters, "newton_fallbacks": stats[1], "clipped_cells": stats[2],
+        "mlp": mlp_info,
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64,
     }
     print(json.dumps(line))
