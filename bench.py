@@ -131,9 +131,10 @@ class ClockSampler:
 OPS_MOMENT_EVAL = 46
 OPS_GRAM_EVAL = 7
 # DRAM bytes per fitted cell (both fits) of newton_kernel, from the ncu
-# capture summarised in profiles/newton_kernel_harris_128x64_v20.md; None
-# until a capture of the current kernel exists.
-NEWTON_DRAM_BYTES_PER_CELL = None
+# capture summarised in profiles/newton_kernel_harris_128x64_v16.md
+# (7.1 MB read + 14.3 MB written for 8192 cells; mostly the kernel's local
+# memory, i.e. register spills); None once the kernel has changed since.
+NEWTON_DRAM_BYTES_PER_CELL = (7.117824e6 + 14.277888e6) / 8192
 
 
 def alu_peak_tops():
