@@ -168,6 +168,23 @@ def newton_roofline(cfg, stats, fit_ms, launches):
             "evaluations": {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7]}}
 
 
+def slowest(seconds, dist=None, device="cpu"):
+    """The replicas' wall time: the largest value over all ranks (identity
+    without a process group)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank processes the same workload)."""
+    return units_per_rank * steps * world / seconds
+
+
 def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=4096, lr=2e-3):
     """Harvest (inputs, eta* - eta_0) samples from the converged fits of a
     cold-started run, train the network on the GPU, return its weights."""
@@ -336,11 +353,8 @@ def main():
         phase_ms[label] = phase_ms.get(label, 0.0) + e0.elapsed_time(e1)
         count[label] = count.get(label, 0) + 1
     stats = abi.vl_read_stats(sim.ctx, stream)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = cells * args.steps * world / elapsed
+    elapsed = slowest(elapsed, dist, device)
+    value = job_rate(cells, args.steps, world, elapsed)
 
     # ---- roofline of the dominant kernel --------------------------------------
     peak, peak_kind = peaks()
@@ -400,13 +414,9 @@ def main():
                     h.copy_(f, non_blocking=True)
         e1.record(stream)
         barrier_sync()
-        et = e0.elapsed_time(e1) / 1e3
-        if dist:
-            t = torch.tensor([et], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et = slowest(e0.elapsed_time(e1) / 1e3, dist, device)
         nbytes = sum(f.numel() * f.element_size() for f in sim.f)
-        e2e = {"value": cells * ksteps * world / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": job_rate(cells, ksteps, world, et), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ksteps}
 
     nfits = max(1, 2 * cfg.ncell * len(cfg.species) * args.steps)
