@@ -248,6 +248,82 @@ def asym_sheet(nx=1024, ny=512, nv=12, lx=51.2, ly=25.6, mass_ratio=100.0, lam=0
     return cfg
 
 
+def _splitmix64(z):
+    """splitmix64 finaliser of uint64 counters (numpy arrays)."""
+    z = (z + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(0xFFFFFFFFFFFFFFFF)
+    return z ^ (z >> np.uint64(31))
+
+
+def _asym_fields(cfg):
+    """Far-field values of the asymmetric sheet: side 2 (y < 0) dense and
+    cold (n2 = 1, T2 = T_e + T_i = 0.5), side 1 (y > 0) tenuous and hot
+    (n1 = n2 / n_ratio, T1 = t_ratio T2), B_x -> -B2 and B1 = 1, with B2 from
+    equal total pressure n T + B^2 / 2 on both sides."""
+    n2, t2 = 1.0, 0.5
+    n1, t1 = n2 / cfg.n_ratio, t2 * cfg.t_ratio
+    b1 = 1.0
+    b2 = math.sqrt(b1 * b1 + 2.0 * (n1 * t1 - n2 * t2))
+    p0 = n1 * t1 + 0.5 * b1 * b1
+    return n1, t1, b1, n2, t2, b2, p0
+
+
+def _asym_Az(cfg, x, y):
+    n1, t1, b1, n2, t2, b2, p0 = _asym_fields(cfg)
+    lam = cfg.lam
+    a = 0.5 * (b1 + b2) * lam * np.log(np.cosh(y / lam)) + 0.5 * (b1 - b2) * y
+    # X-line perturbation (Gaussian about the origin) and 1e-6 noise from a
+    # counter hash of the corner index (periodic in x) and the seed
+    a = a + cfg.xi * np.exp(-(x * x + y * y) / (4.0 * lam * lam))
+    ci = np.mod(np.rint((x - cfg.x0) / cfg.dx).astype(np.int64), cfg.nx)
+    cj = np.rint((y - cfg.y0) / cfg.dy).astype(np.int64)
+    idx = (cj * cfg.nx + ci).astype(np.uint64) + np.uint64(cfg.seed) * np.uint64(1 << 32)
+    u = (_splitmix64(idx) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return a + 1e-6 * cfg.dy * (2.0 * u - 1.0)
+
+
+def asym_profiles(cfg, y):
+    """n(y), total temperature T(y) and B_x(y) of the unperturbed sheet:
+    B_x = (B1 + B2)/2 tanh(y/lam) + (B1 - B2)/2, T = (T1 + T2)/2 +
+    (T1 - T2)/2 tanh(y/lam), and n = (p0 - B_x^2/2) / T (exact pressure
+    balance)."""
+    n1, t1, b1, n2, t2, b2, p0 = _asym_fields(cfg)
+    th = np.tanh(y / cfg.lam)
+    bx = 0.5 * (b1 + b2) * th + 0.5 * (b1 - b2)
+    tt = 0.5 * (t1 + t2) + 0.5 * (t1 - t2) * th
+    return (p0 - 0.5 * bx * bx) / tt, tt, bx
+
+
+def asym_state(cfg: Config, dtype=np.float64):
+    """Initial f per species of the asymmetric sheet: Maxwellians with the
+    local density and temperature (T_i / T_e = 5 everywhere), drifting in z
+    with the current j_z = -dB_x/dy shared as in the Harris sheet."""
+    X, Y = _cell_centres(cfg)
+    n, tt, bx = asym_profiles(cfg, Y)
+    n1, t1, b1, n2, t2, b2, p0 = _asym_fields(cfg)
+    jz = -0.5 * (b1 + b2) / cfg.lam / np.cosh(Y / cfg.lam) ** 2
+    out = []
+    for sp in cfg.species:
+        frac = 1.0 / 6.0 if sp.name == "e" else 5.0 / 6.0
+        th = frac * tt / sp.m
+        uz = (frac * jz / n) * (1.0 if sp.name == "i" else -1.0)
+        vx, vy, vz = sp.vcentres(0), sp.vcentres(1), sp.vcentres(2)
+        f = np.empty((cfg.ny, cfg.nx, sp.nv[2], sp.nv[1], sp.nv[0]), dtype=dtype)
+        for j in range(cfg.ny):
+            tj = th[j][:, None, None, None]
+            norm = (n[j] / (2 * math.pi * th[j]) ** 1.5)[:, None, None, None]
+            e = ((vz[None, :, None, None] - uz[j][:, None, None, None]) ** 2 + vy[None, None, :, None] ** 2 +
+                 vx[None, None, None, :] ** 2)
+            f[j] = (norm * np.exp(-e / (2 * tj))).astype(dtype)
+        out.append(f)
+    return out
+
+
+def asym_yee(cfg: Config):
+    return yee_from_Az(cfg, _asym_Az, bz=cfg.bguide)
+
+
 # -------------------------------------------------------------- random data ---
 
 def random_blocks(shape, seed, low=0.0, high=1.0, dtype=np.float64):

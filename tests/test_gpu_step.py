@@ -106,3 +106,20 @@ def test_landau_damping_on_gpu(gpu, orc):
     assert abs(sim.f_host(0).sum() - m0) <= 1e-12 * m0
     assert abs(sim.total_energy() - E0) <= 1e-5 * E0
     sim.close()
+
+
+def test_asymmetric_sheet_fp64_steps_match_oracle(gpu, orc):
+    """The asymmetric (magnetopause-like) sheet, downscaled: density ratio 10,
+    temperature ratio 3, guide field 0.1, m_i/m_e = 100; FP64 steps equal
+    the oracle's to 1e-10."""
+    cfg = W.asym_sheet(nx=16, ny=16, nv=8, lx=3.2, ly=6.4, precision=64)
+    cfg.fit_tol = 1e-12
+    f, yee = W.asym_state(cfg), W.asym_yee(cfg)
+    ost, sim = run_both(cfg, f, yee, 2)
+    for k in range(2):
+        ref = ost.f[k]
+        got = sim.f_host(k)
+        assert np.abs(got - ref).max() <= 1e-10 * ref.max(), np.abs(got - ref).max() / ref.max()
+    np.testing.assert_allclose(sim.yee.cpu().numpy(), ost.yee, rtol=0, atol=1e-10 * np.abs(ost.yee).max())
+    assert sim.stats()[3] == 0
+    sim.close()
