@@ -283,7 +283,11 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
         if (wall && !(dmax + 3.0 <= (double)d.ny))
             return fail(ctx, VL_EINVAL, "y sweep: |v_y| dt / dy = %g too large for %d rows between walls", dmax, d.ny);
     }
-    if (wall) {
+    if (wall && a.nvy % 4 == 0) {
+        a.mode = 2;
+        a.ncol = 4 * a.nvx;
+        a.nchunks = d.nv[s][2] * (a.nvy / 4);
+    } else if (wall) {
         a.mode = 1;
         a.ncol = 2 * a.nvx;
         a.nchunks = d.nv[s][2] * ((a.nvy + 1) / 2);

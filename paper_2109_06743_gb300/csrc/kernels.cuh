@@ -15,7 +15,7 @@ struct SpaceSweepArgs {
     long long V;            // velocity block size
     int wall;               // reflecting walls (mirror rows use the v_y-mirrored column)
     int ncol, nchunks;      // velocity columns per tile, tiles per line
-    int mode;               // 0: contiguous columns, 1: v_y mirror pairs
+    int mode;               // 0: contiguous columns, 1: v_y mirror pairs, 2: two v_y rows + mirrors
     int vec;                // column runs 16-byte aligned: stage tiles with cp.async
     int nbuf;               // tile buffers in shared memory (2: prefetch the next tile)
     int nvx, nvy;

@@ -2,9 +2,9 @@
 // and Bertrand 2001; Sec. 3.3: reflecting walls in y).
 //
 // A tile is one spatial line (a y row for the x sweep, an x column for the y
-// sweep) times W velocity columns: rows along the sweep axis, each row a
-// contiguous run of the velocity block, so every global access is a
-// 64-128 byte segment. Persistent CTAs walk the tiles; each tile is staged in
+// sweep) times W velocity columns: rows along the sweep axis, each row made
+// of contiguous 128-byte runs of the velocity block (with reflecting walls:
+// two adjacent v_y rows and their two mirror rows). Persistent CTAs walk the tiles; each tile is staged in
 // shared memory with 16-byte cp.async copies, double buffered, so the copy of
 // tile t+1 is in flight while tile t is computed. Each thread walks a segment
 // of one column with a sliding window and writes the result straight back to
@@ -45,6 +45,22 @@ __device__ __forceinline__ bool col_vi(const SpaceSweepArgs& a, int chunk, int c
         *vi = v;
         *mcol = col;
         return v < a.V;
+    }
+    if (a.mode == 2) {
+        // reflecting walls: rows j, j + 1 of the lower v_y half and their
+        // mirrors jm - 1, jm (jm = nvy - 1 - j), two contiguous runs of 2 nvx
+        const int nvx = a.nvx, pairs = a.nvy / 4;
+        const int k = chunk / pairs, j = 2 * (chunk % pairs), jm = a.nvy - 1 - j;
+        if (col < 2 * nvx) {
+            const int r = col / nvx;
+            *vi = (k * a.nvy + j) * nvx + col;
+            *mcol = (3 - r) * nvx + col % nvx;
+        } else {
+            const int c2 = col - 2 * nvx, r = c2 / nvx;
+            *vi = (k * a.nvy + jm - 1) * nvx + c2;
+            *mcol = (1 - r) * nvx + c2 % nvx;
+        }
+        return true;
     }
     const int half = (a.nvy + 1) / 2;
     const int k = chunk / half, j = chunk % half;
@@ -169,19 +185,39 @@ __global__ void __launch_bounds__(1024) pfc_space_kernel(SpaceSweepArgs a) {
             const int k1 = min(n, k0 + L);
             if (k0 < k1) {
                 int j = k0 - s;
-                T fm2 = fetch(j - 2), fm1 = fetch(j - 1), f0 = fetch(j), fp1 = fetch(j + 1);
-                T phim = pfc_phi<T>(alpha, A, B, fm2, fm1, f0);
-                for (int k = k0; k < k1; ++k) {
+                T fm1 = fetch(j - 1), f0 = fetch(j), fp1 = fetch(j + 1);
+                T phim = pfc_phi<T>(alpha, A, B, fetch(j - 2), fm1, f0);
+                // output walks the line in the frame's direction
+                T* out = f + base + vi + (long long)(fwd ? k0 : n - 1 - k0) * a.row_stride;
+                const long long os = fwd ? a.row_stride : -a.row_stride;
+                // at step k the window needs the value at frame index k - s + 2:
+                // inside the line for s - 2 <= k <= n - 3 + s, where it is read
+                // straight from the tile with a signed stride; the few steps
+                // outside take the periodic or mirrored value
+                const int ka = max(k0, min(k1, s - 2));
+                const int kb = max(ka, min(k1, n - 2 + s));
+                auto advance = [&](T next) {
                     const T phi = pfc_phi<T>(alpha, A, B, fm1, f0, fp1);
-                    const int i = fwd ? k : n - 1 - k;
-                    f[base + (long long)i * a.row_stride + vi] = f0 - phi + phim;
-                    ++j;
-                    fm2 = fm1;
+                    *out = f0 - phi + phim;
+                    out += os;
                     fm1 = f0;
                     f0 = fp1;
-                    fp1 = fetch(j + 1);
+                    fp1 = next;
                     phim = phi;
+                };
+                int k = k0;
+                for (; k < ka; ++k) advance(fetch(k - s + 2));
+                {
+                    const int ts = fwd ? ncol : -ncol;
+                    const T* src = tile + (fwd ? col : (n - 1) * ncol + col) + (k - s + 2) * ts;
+#pragma unroll 4
+                    for (; k < kb; ++k) {
+                        const T next = *src;
+                        src += ts;
+                        advance(next);
+                    }
                 }
+                for (; k < k1; ++k) advance(fetch(k - s + 2));
             }
         }
         __syncthreads();  // the buffer of tile t is refilled in a later iteration
