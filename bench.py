@@ -134,7 +134,7 @@ OPS_GRAM_EVAL = 7
 # capture summarised in profiles/newton_kernel_harris_128x64_v16.md
 # (7.1 MB read + 14.3 MB written for 8192 cells; mostly the kernel's local
 # memory, i.e. register spills); None once the kernel has changed since.
-NEWTON_DRAM_BYTES_PER_CELL = (7.117824e6 + 14.277888e6) / 8192
+NEWTON_DRAM_BYTES_PER_CELL = None
 
 
 def alu_peak_tops():
