@@ -221,6 +221,65 @@ def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=409
     return w, info
 
 
+def subdomain_accuracy(mlp_w, device, steps=2, sample=(64, 32)):
+    """Accuracy of the timed form (FP32 f, warm-started fits) against the
+    FP64 oracle on a 64 x 32 x 16^3 subdomain with the workload's dx, dv and
+    dt: relative L1 error of f, the largest moment error relative to the
+    moment's absolute scale sum |v^alpha| f dv^3, and both total-energy drifts; the oracle's own time is
+    the CPU baseline (one host core)."""
+    import numpy as np
+
+    import oracle
+    from oracle.step import OracleState
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300 import workloads as W
+    from paper_2109_06743_gb300.driver import Simulation
+    oracle.build()
+    nx, ny = sample
+    cfg = W.harris(nx=nx, ny=ny, nv=16, lx=25.6 * nx / 512, ly=12.8 * ny / 256, precision=32)
+    f64 = W.harris_state(cfg)
+    f32 = [x.astype(np.float32) for x in f64]
+    yee = W.harris_yee(cfg)
+    sim = Simulation(cfg, f32, None, yee, device=device)
+    if mlp_w is not None:
+        abi.mlp_set_weights(sim.ctx, mlp_w)
+    ost = OracleState(cfg, [x.astype(np.float64) for x in f32], None, yee)
+    e0_gpu, e0_or = sim.total_energy(), ost.total_energy()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ost.step(cfg.dt)
+    t_or = time.perf_counter() - t0
+    for _ in range(steps):
+        sim.step(use_mlp=mlp_w is not None)
+    l1, mom = [], []
+    for k in range(len(cfg.species)):
+        a, b = sim.f_host(k), ost.f[k]
+        l1.append(float(np.abs(a - b).sum() / np.abs(b).sum()))
+        mg = sim.mom_t[k].cpu().numpy()
+        mo = oracle.moments(ost.f[k], ost.g, ost.sps[k])
+        # scale of moment alpha: sum |v^alpha| f dv^3 (odd moments vanish by symmetry)
+        sp = cfg.species[k]
+        vs = [np.abs(sp.vcentres(ax)) for ax in range(3)]
+        fb = ost.f[k].reshape(cfg.ncell, sp.nv[2], sp.nv[1], sp.nv[0])
+        dv3 = float(np.prod([(sp.vmax[ax] - sp.vmin[ax]) / sp.nv[ax] for ax in range(3)]))
+        powers = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
+                  (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1),
+                  (0, 1, 2), (0, 0, 3)]
+        scale = np.stack([np.einsum("czyx,x,y,z->c", fb, vs[0] ** a, vs[1] ** b, vs[2] ** c_) * dv3
+                          for a, b, c_ in powers], axis=1) + 1e-300
+        mom.append(float((np.abs(mg - mo) / scale).max()))
+    e1_gpu, e1_or = sim.total_energy(), ost.total_energy()
+    sim.close()
+    cells = cfg.phase_cells() * steps
+    return {"subdomain": "%dx%d x 16^3 per species, 2 species, %d steps, dx, dv, dt of the workload" % (nx, ny, steps),
+            "f_l1_rel_error": max(l1), "moment_max_rel_error": max(mom),
+            "energy_drift_gpu": (e1_gpu - e0_gpu) / e0_gpu, "energy_drift_oracle": (e1_or - e0_or) / e0_or,
+            "energy_gpu_vs_oracle": (e1_gpu - e1_or) / e1_or}, {
+        "value": cells / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": "%d oracle steps of the Harris sheet on a %dx%d x 16^3 subdomain (2 species, %d cells, same dx, "
+                  "dv, dt as the workload), FP64, one host core, %.1f s" % (steps, nx, ny, cfg.phase_cells(), t_or)}
+
+
 def cpu_baseline(steps=1, sample=(32, 16)):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     a 32x16 spatial subdomain with the workload's dx, dv (both species),
@@ -453,7 +512,7 @@ def main():
 
     if rank != 0:
         return 0
-    cb = None if args.no_cpu else cpu_baseline()
+    acc, cb = (None, None) if args.no_cpu else subdomain_accuracy(mlp_w, device)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -469,7 +528,7 @@ def main():
         "phases_ms_per_step": {k: v / args.steps for k, v in sorted(phase_ms.items())},
         "hbm_phases": rows,
         "newton_iterations_per_fit": fit_iters, "newton_fallbacks": stats[1], "clipped_cells": stats[2],
-        "mlp": mlp_info,
+        "mlp": mlp_info, "accuracy_vs_fp64_oracle": acc,
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64,
     }
     print(json.dumps(line))
