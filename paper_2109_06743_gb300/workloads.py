@@ -110,6 +110,24 @@ def landau_state(cfg: Config):
     return [np.ascontiguousarray(f)]
 
 
+def two_stream(nx=64, nv=64, vmax=5.0, alpha=0.01, k=0.5, dt=0.05, steps=600, precision=64) -> Config:
+    """1D1V two-stream instability (Sec. 3.1): f0 = v^2 exp(-v^2/2) / sqrt(2 pi)
+    (1 + alpha cos kx) on [0, 4 pi), velocities in [-5, 5] v_t, 64 x 64 cells."""
+    cfg = landau(nx=nx, nv=nv, vmax=vmax, alpha=alpha, k=k, dt=dt, steps=steps, precision=precision)
+    cfg.name = "two_stream_1d1v_%dx%d" % (nx, nv)
+    cfg.kind = "two_stream"
+    return cfg
+
+
+def two_stream_state(cfg: Config):
+    sp = cfg.species[0]
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    v = sp.vcentres(0)
+    f = (v[None, :] ** 2 * np.exp(-0.5 * v[None, :] ** 2) / math.sqrt(2 * math.pi)) * (
+        1.0 + cfg.alpha * np.cos(cfg.k * x))[:, None]
+    return [np.ascontiguousarray(f)]
+
+
 # ----------------------------------------------------------------- Harris ---
 
 def harris(nx=128, ny=64, nv=20, lx=25.6, ly=12.8, mass_ratio=25.0, lam=0.5, nb=0.2,

@@ -1,0 +1,108 @@
+"""Physics of the GPU path beyond linear Landau damping (Sec. 3.1), and the
+standard-PFC ablation (moment fitting off).
+
+* Two-stream instability (64 x 64, v in [-5, 5], [0, 4 pi)): the field at
+  k = 0.5 grows at the rate of the dispersion root (within 6%, fitted over
+  the exponential phase, 0.01 < |E_k| < 0.1), mass is conserved to 1e-12,
+  and the fitted and standard PFC solvers give the same f at t = 30 (L1
+  difference below 2%; measured 0.5%), as the paper reports.
+* Non-linear Landau damping (32 x 64, v in [-6, 6], alpha = 0.5): mass to
+  1e-12, the fitted solver conserves total energy at least five times better
+  than standard PFC (measured 0.08% vs 1.4% at t = 30), and the first three
+  peaks of the damped field energy agree between the two within 10%.
+* Coarse 2D3V wave (12^3 velocity cells): standard PFC heats by more than 1%
+  in ten steps while moment fitting keeps the energy to 1e-6 (the paper's
+  coarse-grid claim, Sec. 3.2-3.3), on the GPU as in the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_2109_06743_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2109_06743_gb300 import build
+    build.build()
+    return torch
+
+
+def run_1d(cfg, f0, fit, steps):
+    from paper_2109_06743_gb300.driver import Simulation
+    sim = Simulation(cfg, f0, fit=fit)
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    E0, m0 = sim.total_energy(), f0[0].sum()
+    ts, amps, ee = [], [], []
+    for _ in range(steps):
+        sim.step()
+        e = sim.eb[:, 0].cpu().numpy()
+        ts.append(sim.time)
+        amps.append(2 * abs(np.sum(e * np.exp(-1j * cfg.k * x))) / cfg.nx)
+        ee.append(0.5 * (e ** 2).sum() * cfg.dx)
+    f = sim.f_host(0)
+    out = {"t": np.array(ts), "amp": np.array(amps), "ee": np.array(ee), "f": f,
+           "dE": (sim.total_energy() - E0) / E0, "dm": (f.sum() - m0) / m0}
+    sim.close()
+    return out
+
+
+def test_two_stream_growth_rate_and_agreement_with_standard_pfc(gpu):
+    from test_oracle_physics import two_stream_root
+    cfg = W.two_stream()
+    f0 = W.two_stream_state(cfg)
+    fit = run_1d(cfg, f0, True, 600)
+    std = run_1d(cfg, f0, False, 600)
+    _, gamma, _ = two_stream_root(cfg.k)
+    # exponential phase: after the initial transient (minimum of |E_k| before
+    # t = 8), from |E_k| = 0.01 to 0.1
+    a = fit["amp"]
+    low = int(np.argmin(a[: int(8 / cfg.dt)]))
+    first = low + int(np.argmax(a[low:] > 0.01))
+    last = first + int(np.argmax(a[first:] > 0.1))
+    rate = np.polyfit(fit["t"][first:last], np.log(a[first:last]), 1)[0]
+    assert last - first > 20 and abs(rate - gamma) / gamma < 0.06, (rate, gamma)
+    assert abs(fit["dm"]) < 1e-12 and abs(std["dm"]) < 1e-12
+    l1 = np.abs(fit["f"] - std["f"]).sum() / np.abs(std["f"]).sum()
+    assert l1 < 0.02, l1
+
+
+def test_nonlinear_landau_fitting_conserves_energy_better(gpu):
+    cfg = W.landau(nx=32, nv=64, vmax=6.0, alpha=0.5, steps=600)
+    f0 = W.landau_state(cfg)
+    fit = run_1d(cfg, f0, True, 600)
+    std = run_1d(cfg, f0, False, 600)
+    assert abs(fit["dm"]) < 1e-12 and abs(std["dm"]) < 1e-12
+    assert abs(fit["dE"]) < 5e-3 and 5 * abs(fit["dE"]) < abs(std["dE"]), (fit["dE"], std["dE"])
+
+    def peaks(r):
+        ee = r["ee"][: int(15 / cfg.dt)]
+        return np.array([ee[i] for i in range(1, len(ee) - 1) if ee[i] > ee[i - 1] and ee[i] >= ee[i + 1]][:4])
+
+    # the first three peaks of the field energy agree (measured within 6%);
+    # by the fourth (1% of the first) the two solvers' dissipation differs
+    pf, ps = peaks(fit), peaks(std)
+    assert len(pf) == 4 and len(ps) == 4
+    assert np.all(np.abs(pf[:3] - ps[:3]) <= 0.1 * ps[:3]), (pf, ps)
+
+
+def test_standard_pfc_heats_coarse_grid_and_fitting_does_not(gpu):
+    from paper_2109_06743_gb300.driver import Simulation
+    cfg = W.wave2d(steps=10, precision=64)
+    drift = {}
+    for fit in (True, False):
+        sim = Simulation(cfg, W.wave2d_state(cfg), None, W.wave2d_yee(cfg), fit=fit)
+        E0 = sim.total_energy()
+        m0 = [sim.f_host(k).sum() for k in range(2)]
+        for _ in range(cfg.steps):
+            sim.step()
+        drift[fit] = (sim.total_energy() - E0) / E0
+        for k in range(2):
+            assert abs(sim.f_host(k).sum() - m0[k]) <= 1e-12 * m0[k]
+        sim.close()
+    assert abs(drift[True]) < 1e-6, drift
+    assert drift[False] > 1e-2, drift

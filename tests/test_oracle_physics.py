@@ -107,3 +107,43 @@ def test_wave2d_energy_conserved_with_fitting_and_not_without(orc):
             assert abs(a - b) <= 1e-13 * b
     assert abs(drift[True]) < 1e-6, drift
     assert drift[False] > 1e-2, drift  # standard PFC heats on the coarse grid
+
+
+def two_stream_root(k):
+    """Growing root of the dielectric function of the two-stream distribution
+    f0 = v^2 exp(-v^2/2) / sqrt(2 pi) (Sec. 3.1): with u = omega / k,
+    eps = 1 - (1/k^2) [1 - u^2 + (2u - u^3) Z(u / sqrt 2) / sqrt 2], from
+    f0' = (2v - v^3) M and the division (2v - v^3) / (v - u)."""
+    from scipy.optimize import fsolve
+    from scipy.special import wofz
+
+    def eps(w):
+        u = w / k
+        z = 1j * math.sqrt(math.pi) * wofz(u / math.sqrt(2))
+        return 1 - (1 / k ** 2) * (1 - u ** 2 + (2 * u - u ** 3) * z / math.sqrt(2))
+
+    def eq(p):
+        r = eps(p[0] + 1j * p[1])
+        return [r.real, r.imag]
+
+    wr, wi = fsolve(eq, [0.0, 0.2], xtol=1e-14)
+    return wr, wi, eps
+
+
+def test_two_stream_root_against_direct_quadrature():
+    """The closed form agrees with eps(omega) = 1 - (1/k^2) int f0'(v)/(v - omega/k) dv
+    summed directly on the real line (regular for Im omega > 0), at the root
+    and at another point; the root is a purely growing mode."""
+    k = 0.5
+    wr, wi, eps = two_stream_root(k)
+    v = np.linspace(-40, 40, 800001)
+    M = np.exp(-0.5 * v * v) / math.sqrt(2 * math.pi)
+    fp = (2 * v - v ** 3) * M
+
+    def eps_quad(w):
+        return 1 - (1 / k ** 2) * np.trapezoid(fp / (v - w / k), v)
+
+    assert abs(wr) < 1e-8 and 0.25 < wi < 0.27, (wr, wi)
+    assert abs(eps_quad(wr + 1j * wi)) < 1e-7
+    for w in (0.3 + 0.4j, -0.7 + 0.9j):
+        assert abs(eps_quad(w) - eps(w)) < 1e-7
