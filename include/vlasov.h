@@ -102,6 +102,20 @@ const char* vl_last_error(const vl_ctx* ctx);
  * and Sec. 3.3 (reflecting walls). |v| dt / dx may exceed 1. */
 vl_status pfc_advect_x(vl_ctx* ctx, int species, int axis, double dt, vl_stream_t stream);
 
+/* Spatial PFC sweeps of species s along x and then along y (the two
+ * pfc_advect_x calls of the Vlasov step, Sec. 2.1 directional splitting;
+ * Sec. 3.3 walls), fused into one pass that reads f once and writes it once.
+ * Out of place: reads the species' current f and writes the result to f_out
+ * (same layout, size and precision; caller-owned device memory that must not
+ * overlap it and is aligned to the element size). On success the context's f
+ * for species s becomes f_out, and the previous buffer is no longer used by
+ * the context (the caller may pass it as f_out of the next call). The result
+ * is element for element that of pfc_advect_x(x) then pfc_advect_x(y); the
+ * same limits apply (VL_EINVAL). Grids whose nx or ny is not a multiple of 8,
+ * or whose y shift exceeds 6 cells, take the two single-axis sweeps in place
+ * followed by a device copy into f_out, with the same result. */
+vl_status pfc_advect_xy(vl_ctx* ctx, int species, double dt, void* f_out, vl_stream_t stream);
+
 /* Velocity-space PFC advection of species s under (q/m)(E + v x B) over dt
  * with the cell-centred fields eb, zero-flux at the velocity box (Sec. 2.1).
  * 2D3V: the Boris map of each cell is factored into nshear single-axis
@@ -238,8 +252,11 @@ vl_status mlp_grad(vl_ctx* ctx, const float* samples_dev, long long n, float* gr
  * out[4] double-float moment evaluations (recurrence path), out[5] FP32
  * Jacobian (Gram) evaluations, out[6] evaluations with one FP64 exponential
  * per velocity cell (wide exponent range), out[7] Newton steps with the
- * FP64 Jacobian. Synchronises the stream. */
-#define VL_NSTATS 8
+ * FP64 Jacobian; out[8] asynchronous tile copies whose wait ran out of time
+ * (the fused spatial sweep gives up on such a tile and leaves it unwritten:
+ * any nonzero value means the result of that call is invalid). Synchronises
+ * the stream. */
+#define VL_NSTATS 9
 vl_status vl_read_stats(vl_ctx* ctx, long long out[VL_NSTATS], vl_stream_t stream);
 vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream);
 

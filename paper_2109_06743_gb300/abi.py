@@ -13,12 +13,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvlasov.so")
 MAX_SPECIES = 4
-NSTATS = 8  # VL_NSTATS
+NSTATS = 9  # VL_NSTATS
 
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
-            "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
+            "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
             "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
             "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
             "mlp_grad"]
@@ -79,6 +79,7 @@ def lib():
     L.vl_last_error.argtypes = [_vp]
     L.vl_last_error.restype = ctypes.c_char_p
     L.pfc_advect_x.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp]
+    L.pfc_advect_xy.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp]
     L.pfc_advect_v.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp]
     L.pfc_advect_v_static.argtypes = [D, ctypes.c_int, _vp, _vp, ctypes.c_longlong, ctypes.c_double, _vp, _vp]
     L.moments.argtypes = [_vp, ctypes.c_int, _vp, _vp]
@@ -179,6 +180,12 @@ def vlasov_free(ctx):
 
 def pfc_advect_x(ctx, species, axis, dt, stream=None):
     _check(ctx, lib().pfc_advect_x(ctx, species, axis, dt, stream_handle(stream)))
+
+
+def pfc_advect_xy(ctx, species, dt, f_out, stream=None):
+    """x then y sweep, out of place into f_out; the context's f of the
+    species becomes f_out (the caller swaps its buffers)."""
+    _check(ctx, lib().pfc_advect_xy(ctx, species, dt, ptr(f_out), stream_handle(stream)))
 
 
 def pfc_advect_v(ctx, species, dt, mom_out=None, stream=None):

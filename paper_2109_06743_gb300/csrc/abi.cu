@@ -312,6 +312,81 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
     return cuda_check(ctx, vl::launch_pfc_space(a, d.precision, (cudaStream_t)stream), "pfc_advect_x");
 }
 
+vl_status pfc_advect_xy(vl_ctx* ctx, int s, double dt, void* f_out, vl_stream_t stream) {
+    vl_status st = check_species(ctx, s);
+    if (st != VL_OK) return st;
+    const vl_desc& d = ctx->d;
+    if (d.nvdim != 3) return fail(ctx, VL_EINVAL, "pfc_advect_xy needs a 2D3V descriptor");
+    if (!std::isfinite(dt)) return fail(ctx, VL_EINVAL, "dt is not finite");
+    if (!f_out) return fail(ctx, VL_EINVAL, "f_out is NULL");
+    const long long V = vblock_of(d, s);
+    const int es = d.precision == 64 ? 8 : 4;
+    const size_t bytes = (size_t)ncell_of(d) * (size_t)V * es;
+    {
+        const char* a0 = static_cast<const char*>(ctx->f[s]);
+        const char* b0 = static_cast<const char*>(f_out);
+        if (b0 < a0 + bytes && a0 < b0 + bytes) return fail(ctx, VL_EINVAL, "f_out overlaps the species' f");
+        if (reinterpret_cast<uintptr_t>(f_out) % es != 0) return fail(ctx, VL_EINVAL, "f_out is not aligned to its element size");
+    }
+    // the single-axis sweeps' limits, so that both paths accept the same calls
+    for (int ax = 0; ax < 2; ++ax) {
+        const double h = ax == 0 ? d.dx : d.dy;
+        const double vmax = std::fmax(std::fabs(d.vmin[s][ax]), std::fabs(d.vmax[s][ax]));
+        const double dmax = vmax * std::fabs(dt) / h;
+        if (!(dmax < 1.0e6)) return fail(ctx, VL_EINVAL, "displacement of %g cells is not supported", dmax);
+        if (ax == 1 && d.bc_y == 1 && !(dmax + 3.0 <= (double)d.ny))
+            return fail(ctx, VL_EINVAL, "y sweep: |v_y| dt / dy = %g too large for %d rows between walls", dmax, d.ny);
+    }
+    vl::SpaceXYArgs a;
+    a.f_in = ctx->f[s];
+    a.f_out = f_out;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.V = V;
+    a.nvx = d.nv[s][0];
+    a.nvy = d.nv[s][1];
+    a.wall = d.bc_y == 1;
+    a.ncol = 128 / es;
+    a.nchunks = (int)((V + a.ncol - 1) / a.ncol);
+    a.vminx = d.vmin[s][0];
+    a.dvx = dv_of(d, s, 0);
+    a.cx = dt / d.dx;
+    a.vminy = d.vmin[s][1];
+    a.dvy = dv_of(d, s, 1);
+    a.cy = dt / d.dy;
+    // halos: the largest shift along each axis (as the kernels compute it) + 2
+    auto halo = [](double vmin, double dv, double c, int nv, int n, bool periodic) {
+        int smax = 0;
+        for (int i = 0; i < nv; ++i) {
+            double ca = std::fabs((vmin + (i + 0.5) * dv) * c);
+            if (periodic) ca = std::fmod(ca, (double)n);
+            if (!(ca <= (double)n)) ca = (double)n;
+            smax = std::max(smax, (int)std::floor(ca));
+        }
+        return smax + 2;
+    };
+    a.hx = halo(a.vminx, a.dvx, a.cx, a.nvx, d.nx, true);
+    a.hy = halo(a.vminy, a.dvy, a.cy, a.nvy, d.ny, !a.wall);
+    a.counters = ctx->ws.counters;
+    a.tx = d.nx % 32 == 0 ? 32 : (d.nx % 16 == 0 ? 16 : (d.nx % 8 == 0 ? 8 : 0));
+    a.ty = d.ny % 16 == 0 ? 16 : (d.ny % 8 == 0 ? 8 : 0);
+    const long long ntiles = a.tx && a.ty ? (long long)a.nchunks * (d.nx / a.tx) * (d.ny / a.ty) : 0;
+    const bool fused = a.tx && a.ty && a.hy <= 8 && a.hy <= d.ny && ntiles < (1LL << 31);
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (fused) {
+        st = cuda_check(ctx, vl::launch_pfc_space_xy(a, d.precision, cs), "pfc_advect_xy");
+    } else {
+        // grids without 8-cell tiles or with long y shifts: the two in-place
+        // sweeps, then the result moves to f_out
+        st = pfc_advect_x(ctx, s, 0, dt, stream);
+        if (st == VL_OK) st = pfc_advect_x(ctx, s, 1, dt, stream);
+        if (st == VL_OK)
+            st = cuda_check(ctx, cudaMemcpyAsync(f_out, ctx->f[s], bytes, cudaMemcpyDeviceToDevice, cs), "pfc_advect_xy copy");
+    }
+    if (st == VL_OK) ctx->f[s] = f_out;
+    return st;
+}
+
 vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream_t stream) {
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;

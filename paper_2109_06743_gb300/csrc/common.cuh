@@ -44,6 +44,10 @@ struct Workspace {
     float* mlp;           // MLP weights and scratch
 };
 
+// indices of the device counters (vl_read_stats)
+enum { CNT_ITERS = 0, CNT_FALLBACK = 1, CNT_CLIPPED = 2, CNT_INVALID = 3, CNT_EVAL_M = 4, CNT_EVAL_G = 5,
+       CNT_EVAL_SLOW = 6, CNT_PRECISE = 7, CNT_COPY_TIMEOUT = 8 };
+
 __host__ __device__ inline int ifloor(double x) { return (int)floor(x); }
 
 }  // namespace vl

@@ -12,7 +12,6 @@
 
 namespace vl {
 
-enum { CNT_ITERS = 0, CNT_FALLBACK = 1, CNT_CLIPPED = 2, CNT_INVALID = 3 };
 constexpr int kCoef = 16;  // per fit: eta[10], u0[3], sigma[3]
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -24,6 +24,50 @@ struct SpaceSweepArgs {
 };
 cudaError_t launch_pfc_space(const SpaceSweepArgs& a, int precision, cudaStream_t st);
 
+// ---- fused x + y spatial sweep (out of place) ------------------------------
+// Division of 0 <= n < 2^31 by a fixed d >= 1 with a multiply-high (the
+// round-up method of Granlund and Montgomery, 1994): q = (hi(n m) + n) >> l,
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 (mod 2^32).
+struct FastDiv {
+    unsigned m;
+    int l;
+    int d;
+};
+inline FastDiv make_fastdiv(int d) {
+    FastDiv f;
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    f.l = l;
+    f.m = (unsigned)((((1ULL << 32) * ((1ULL << l) - (unsigned long long)d)) / (unsigned long long)d) + 1ULL);
+    f.d = d;
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+    return (int)(((unsigned long long)__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.l);
+}
+#endif
+struct SpaceXYArgs {
+    const void* f_in;       // [ny][nx][V], read only
+    void* f_out;            // [ny][nx][V], must not overlap f_in
+    int nx, ny;
+    long long V;            // velocity block size
+    int nvx, nvy;
+    int wall;               // reflecting walls in y (mirror rows use the v_y-mirrored column)
+    int ncol, nchunks;      // contiguous velocity columns per tile, ceil(V / ncol)
+    int tx, ty;             // spatial tile; tx | nx, ty | ny, both multiples of 8
+    int hx;                 // halo cells on each side in x: largest x shift + 2
+    int hy;                 // halo rows on each side: largest y shift + 2 (<= ny)
+    unsigned long long* counters;  // device counters (lost tile copies)
+    FastDiv div_nvx, div_nvy;      // filled by the launcher
+    FastDiv div_ntx, div_tpc;      // tiles along x, tiles per velocity chunk (TMA path)
+    FastDiv div_bx;                // cells per input box row (TMA path)
+    double vminx, dvx, cx;  // v_x box and dt / dx
+    double vminy, dvy, cy;  // v_y box and dt / dy
+};
+size_t pfc_space_xy_smem(const SpaceXYArgs& a, int precision);
+cudaError_t launch_pfc_space_xy(const SpaceXYArgs& a, int precision, cudaStream_t st);
+
 // ---- velocity-space PFC pass (+ fused moments) -----------------------------
 // Centred-index moments -> physical raw moments: out[o] = sum_t coef[o][t] *
 // im[idx[o][t]], t < nterm[o] (binomial expansion of v = vc + dv xi, times dv^3).

@@ -7,7 +7,8 @@ stream, with no host synchronisation inside a step:
 2D3V (Lie splitting x, y, v):
   1. maxwell_step(dt/2)            current of the fluid state
   2. Q^t                           moments of f^t (from the previous exchange)
-  3. pfc_advect_x(x), pfc_advect_x(y), pfc_advect_v(+ moments -> Q^t+1, V targets)
+  3. pfc_advect_xy (x then y in one out-of-place pass; the two buffers of a
+     species swap roles), pfc_advect_v(+ moments -> Q^t+1, V targets)
   4. fluid_step(dt, Q^t, Q^t+1)    SSP-RK3, Q^t+1/2 = average
   5. moment_fit                    Newton fits, exchange, limiter (+ moments of the new f)
   6. maxwell_step(dt/2)            current of the fitted moments
@@ -22,7 +23,8 @@ from . import abi
 
 
 class Simulation:
-    def __init__(self, cfg, f_list, fluid_list=None, yee=None, device="cuda", stream=None, fit=True):
+    def __init__(self, cfg, f_list, fluid_list=None, yee=None, device="cuda", stream=None, fit=True,
+                 fused_xy=True):
         import torch
 
         self.torch = torch
@@ -30,6 +32,7 @@ class Simulation:
         self.dev = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
         self.fit = fit
+        self.fused_xy = fused_xy and cfg.nvdim == 3
         self.dtype = torch.float32 if cfg.precision == 32 else torch.float64
         nvdim, nc = cfg.nvdim, cfg.ncell
         self.nmom = 4 if nvdim == 1 else 20
@@ -39,6 +42,8 @@ class Simulation:
             for f in f_list:
                 t = torch.as_tensor(np.asarray(f)).reshape(nc, -1).to(device=self.dev, dtype=self.dtype)
                 self.f.append(t.contiguous())
+            # second buffer per species for the out-of-place x+y sweep
+            self.f_spare = [torch.empty_like(t) for t in self.f] if self.fused_xy else None
             self.fluid = torch.zeros((len(cfg.species), nc, self.ncomp), dtype=torch.float64, device=self.dev)
             self.eb = torch.zeros((nc, 6), dtype=torch.float64, device=self.dev)
             if nvdim == 3:
@@ -108,10 +113,15 @@ class Simulation:
             mark("maxwell")
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
             for k in range(ns):
-                mark("x_sweep")
-                abi.pfc_advect_x(ctx, k, 0, dt, s)
-                mark("y_sweep")
-                abi.pfc_advect_x(ctx, k, 1, dt, s)
+                if self.fused_xy:
+                    mark("xy_sweep")
+                    abi.pfc_advect_xy(ctx, k, dt, self.f_spare[k], s)
+                    self.f[k], self.f_spare[k] = self.f_spare[k], self.f[k]
+                else:
+                    mark("x_sweep")
+                    abi.pfc_advect_x(ctx, k, 0, dt, s)
+                    mark("y_sweep")
+                    abi.pfc_advect_x(ctx, k, 1, dt, s)
                 mark("v_pass")
                 abi.pfc_advect_v(ctx, k, dt, self.mom_t1[k], s)
         if self.fit:

@@ -1,0 +1,67 @@
+"""The C-ABI boundary without a GPU: libvlasov builds for sm_103a, loads,
+and exports exactly the entry points that include/vlasov.h declares (each
+bound in the Python layer with the same name); the host-only calls
+(workspace sizing, descriptor validation, error text) answer correctly.
+No call here launches a kernel."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2109_06743_gb300 import abi
+from paper_2109_06743_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(__file__), "..", "include", "vlasov.h")
+
+
+def declared():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\([^;{]*\)\s*;", src, flags=re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("nvcc not available")
+    from paper_2109_06743_gb300 import build
+    path = build.build()
+    assert os.path.exists(path)
+    return abi.lib()
+
+
+def test_header_declarations_are_exported_and_bound(lib):
+    names = declared()
+    assert len(names) >= 20 and len(set(names)) == len(names)
+    assert set(names) == set(abi.EXPORTED)
+    for n in names:
+        assert getattr(lib, n) is not None
+    nm = shutil.which("nm")
+    if nm:
+        out = subprocess.run([nm, "-D", "--defined-only", abi.LIB_PATH], capture_output=True, text=True).stdout
+        text = {line.split()[-1] for line in out.splitlines() if " T " in line}
+        public = {t for t in text if not t.startswith("_")}
+        # no undeclared C entry points (C++ symbols are mangled and start with _)
+        assert public == set(names), public ^ set(names)
+
+
+def test_workspace_sizing_and_validation_on_host(lib):
+    cfg = W.harris(nx=16, ny=8, nv=8, lx=3.2, ly=1.6)
+    d = abi.make_desc(cfg)
+    nb = abi.vlasov_work_bytes(d)
+    nc = cfg.ncell
+    # at least the shear tables (20 doubles per cell) and two fits of 10
+    # parameters per cell
+    assert nb >= nc * 20 * 8 + 2 * nc * 10 * 8
+    bad = abi.make_desc(cfg)
+    bad.nx = 0
+    assert abi.vlasov_work_bytes(bad) == 0
+    assert b"nx" in lib.vl_last_error(None)
+    bad = abi.make_desc(cfg)
+    bad.precision = 16
+    assert abi.vlasov_work_bytes(bad) == 0
+    bad = abi.make_desc(cfg)
+    bad.vmin[0][1] = bad.vmin[0][1] * 0.5  # walls need a box symmetric in v_y
+    assert abi.vlasov_work_bytes(bad) == 0
+    assert isinstance(lib.vl_last_error(None), bytes)

@@ -73,6 +73,61 @@ def test_space_sweep(gpu, orc, precision, axis, bc_y, cfl):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("bc_y", [1, 0])
+@pytest.mark.parametrize("cfl", [0.37, 2.3])
+@pytest.mark.parametrize("grid", [(64, 16, 8), (32, 8, 12), (48, 16, 8), (24, 8, 12), (20, 12, 8)])
+def test_fused_xy_sweep(gpu, orc, precision, bc_y, cfl, grid):
+    """pfc_advect_xy (one out-of-place pass) against the oracle's x then y
+    sweeps, and against the two single-axis GPU sweeps to rounding (the two
+    kernels contract multiply-adds differently). Grids: 64 x 16 and 32 x 8
+    take the TMA kernel (32 x 8 tiles; interior, x-wrapped and wall tiles;
+    a 32 x 8 grid is one tile wrapped on every side) unless the y shift
+    needs halos above 4 rows; 48 x 16 and 24 x 8 the generic fused kernel;
+    20 x 12 (not a multiple of 8) the single-axis fallback with a copy."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    torch = gpu
+    nx, ny, nv = grid
+    cfg = small_harris(nx=nx, ny=ny, nv=nv, precision=precision, bc_y=bc_y)
+    V = nv ** 3
+    f0 = [cast(W.random_blocks((cfg.ncell, V), 200 + k) ** 3, precision) for k in range(2)]
+    r = AbiRunner(cfg, f0)
+    r2 = AbiRunner(cfg, f0)
+    g = oracle_grid(orc, cfg)
+    for k, sp in enumerate(cfg.species):
+        dt = cfl * min(cfg.dx, cfg.dy) / abs(sp.vmin[0])
+        if bc_y == 1:
+            dt = min(dt, 0.9 * (ny - 3) * cfg.dy / abs(sp.vmin[1]))
+        out = torch.full_like(r.f[k], float("nan"))
+        abi.pfc_advect_xy(r.ctx, k, dt, out)
+        abi.pfc_advect_x(r2.ctx, k, 0, dt)
+        abi.pfc_advect_x(r2.ctx, k, 1, dt)
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        ref = f0[k].copy()
+        orc.advect_space(ref, g, oracle_species(orc, sp), 0, dt)
+        orc.advect_space(ref, g, oracle_species(orc, sp), 1, dt)
+        tol = (1e-12 if precision == 64 else 4e-6) * ref.max()
+        assert np.abs(got - ref).max() <= tol, (k, np.abs(got - ref).max(), tol)
+        sep = r2.f_np(k)
+        assert np.abs(got - sep).max() <= (1e-14 if precision == 64 else 1e-6) * ref.max()
+        assert abs(got.sum() - f0[k].sum()) <= (1e-13 if precision == 64 else 2e-6) * f0[k].sum()
+        # the context now works on `out`: a second call moves f back into the
+        # first buffer and equals two more single-axis sweeps
+        abi.pfc_advect_xy(r.ctx, k, dt, r.f[k])
+        abi.pfc_advect_x(r2.ctx, k, 0, dt)
+        abi.pfc_advect_x(r2.ctx, k, 1, dt)
+        assert np.abs(r.f_np(k) - r2.f_np(k)).max() <= (1e-14 if precision == 64 else 2e-6) * ref.max()
+    assert abi.vl_read_stats(r.ctx)[8] == 0  # no tile copy ran out of time
+    with pytest.raises(abi.VlasovError):
+        abi.pfc_advect_xy(r.ctx, 0, 0.01, r.f[0])  # f_out is the current f
+    with pytest.raises(abi.VlasovError):
+        abi.pfc_advect_xy(r.ctx, 0, 0.01, r.f[0][1:])  # overlapping
+    r.close()
+    r2.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("nshear", [5, 3])
 @pytest.mark.parametrize("nv", [8, 12])
 def test_velocity_pass_and_fused_moments(gpu, orc, precision, nshear, nv):
