@@ -47,13 +47,14 @@ UNIT = "cell-updates/s"
 WORKLOADS = {
     # name: (nx, ny, nv, lx, ly)  -- Harris sheet, both species
     "harris_512x256_v16": (512, 256, 16, 25.6, 12.8),
+    "harris_256x128_v16": (256, 128, 16, 25.6, 12.8),
     "harris_128x64_v20": (128, 64, 20, 25.6, 12.8),
     "harris_128x64_v16": (128, 64, 16, 25.6, 12.8),
 }
 # warm-start network: trained on the fits of a smaller run with the same
 # velocity grid (the network's inputs are in units of the velocity cells)
-TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_128x64_v20": "harris_128x64_v20",
-              "harris_128x64_v16": "harris_128x64_v16"}
+TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "harris_128x64_v16",
+              "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16"}
 
 
 def make_cfg(name, precision=32):
