@@ -88,7 +88,10 @@ size_t vlasov_work_bytes(const vl_desc* desc);
  * fields (2D3V; may be NULL for 1D1V), eb_dev the cell-centred fields,
  * work_dev/work_bytes the workspace (at least vlasov_work_bytes(desc), 256-byte
  * aligned). All pointers are device pointers owned by the caller. Validates
- * the descriptor (Sec. 3.3 walls need a velocity box symmetric in v_y). */
+ * the descriptor (Sec. 3.3 walls need a velocity box symmetric in v_y).
+ * f_dev, or any entry of it, may be NULL for a context that only runs the
+ * fluid and field calls (the stand-alone fluid model): the calls that need
+ * f then return VL_EINVAL. */
 vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev,
                       double* yee_dev, double* eb_dev, void* work_dev,
                       size_t work_bytes, vl_ctx** out);
@@ -186,6 +189,19 @@ vl_status moment_fit_exchange(vl_ctx* ctx, int species, const double* vmom,
  * are the cell-centred fields of the context, frozen over the step. */
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t,
                      const double* const* mom_t1, vl_stream_t stream);
+
+/* The stand-alone ten-moment fluid model with the gradient heat-flux closure
+ * (Sec. 2.3, Eq. "gradient closure"): one SSP-RK3 step of length dt of every
+ * species' fluid state, E and B frozen at the context's cell-centred fields.
+ * The third moment in the flux is that of the Maxwellian with the state's
+ * n, u and E2 (zero heat flux), and the heat flux enters as
+ * -(1/m) div Q = (chi / k_s0) n v_t lap(theta) in the second-moment equation,
+ * theta = E2/n - u u, v_t = sqrt(tr(theta)/3), chi = 2 sqrt(2/pi) and
+ * k_s0 = 1/d_s with d_s = sqrt(m_s/(n0 q_s^2)) at the reference density
+ * n0 = 1 (mu0 = 1). No kinetic moments are used; with maxwell_step(h, NULL)
+ * for the fields (current of the fluid state) it is the paper's fluid solver.
+ * 2D3V only (VL_EINVAL otherwise); uses the workspace's fluid stage buffers. */
+vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream);
 
 /* Field update. 2D3V: one leapfrog Yee step of length h (B h/2, E h, B h/2)
  * with the current sum_s q_s n_s u_s taken from mom[s] (raw moments) or, if

@@ -15,6 +15,7 @@ mathematics fix; see the module docstrings there.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -103,6 +104,10 @@ def lib():
             L.or_maxwellian_grid.restype = None
             L.or_moment_fit.argtypes = [_dp, G, S, _dp, ctypes.c_double, ctypes.c_int, _lp]
             L.or_fluid_step.argtypes = [_dp, G, S, _dp, _dp, _dp, _dp, ctypes.c_double]
+            L.or_fluid_step_closure.argtypes = [_dp, G, S, _dp, ctypes.c_double, ctypes.c_double]
+            L.or_fluid_rhs_closure.argtypes = [_dp, G, S, _dp, ctypes.c_double, _dp]
+            L.or_maxwellian_e3.argtypes = [_dp, _dp]
+            L.or_maxwellian_e3.restype = None
             L.or_maxwell.argtypes = [_dp, G, _dp, ctypes.c_double, ctypes.c_double]
             L.or_fields_to_centres.argtypes = [_dp, G, _dp]
             L.or_fields_to_centres.restype = None
@@ -198,6 +203,43 @@ def fluid_step(U, grid, sp, Q0, Qh, Q1, EB, dt):
     args = [np.ascontiguousarray(a, dtype=np.float64) for a in (Q0, Qh, Q1, EB)]
     _check(lib().or_fluid_step(_d(U), ctypes.byref(grid), ctypes.byref(sp), *[_d(a) for a in args], dt),
            "fluid_step")
+
+
+CHI = 2.0 * math.sqrt(2.0 / math.pi)  # Sec. 2.3, after Hammett and Perkins
+
+
+def closure_chi_k0(q, m, n0=1.0):
+    """chi / k_s0 of the gradient closure (Sec. 2.3): k_s0 = 1/d_s with the
+    inertial length d_s = sqrt(m_s / (mu0 n0 q_s^2)) at the reference
+    density n0 of the normalisation (mu0 = 1)."""
+    return CHI * math.sqrt(m / (n0 * q * q))
+
+
+def fluid_step_closure(U, grid, sp, EB, dt, chi_k0):
+    """One SSP-RK3 step of the stand-alone ten-moment fluid with the gradient
+    heat-flux closure of Sec. 2.3 (in place on U; 2D3V)."""
+    EB = np.ascontiguousarray(EB, dtype=np.float64)
+    _check(lib().or_fluid_step_closure(_d(U), ctypes.byref(grid), ctypes.byref(sp), _d(EB), dt, chi_k0),
+           "fluid_step_closure")
+
+
+def fluid_rhs_closure(U, grid, sp, EB, chi_k0):
+    """The semi-discrete right-hand side L(U) of the closure model."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    EB = np.ascontiguousarray(EB, dtype=np.float64)
+    out = np.zeros_like(U)
+    _check(lib().or_fluid_rhs_closure(_d(U), ctypes.byref(grid), ctypes.byref(sp), _d(EB), chi_k0, _d(out)),
+           "fluid_rhs_closure")
+    return out
+
+
+def maxwellian_e3(u):
+    """Third moment int v v v f of the closure model for one state
+    (n, nu_a, E2_ab) (order xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(10)
+    lib().or_maxwellian_e3(_d(u), _d(out))
+    return out
 
 
 def maxwell(yee, grid, J, h, c):

@@ -100,6 +100,10 @@ static double fetch(const fl_ctx* c, const double* A, int stride, int comp,
     return sgn * A[((long)iy * g->nx + ix) * stride + comp];
 }
 
+static double fetch_state(const fl_ctx* c, const double* U, int comp, int ix, int iy) {
+    return fetch(c, U, c->ncomp, comp, ix, iy, 0);
+}
+
 /* flux component k (of ncomp) in direction dir from state u and third
  * moments q */
 static double flux_comp(int d, int dir, int k, const double* u, const double* q) {
@@ -126,7 +130,38 @@ static double wave_speed(int d, int dir, const double* u) {
     return fabs(ud) + sqrt(3.0 * th);
 }
 
-/* semi-discrete right-hand side L(U) */
+/* Gradient-closure model (Sec. 2.3): the third moment E3 = int v v v f of a
+ * state with zero heat flux, i.e. of the Maxwellian with the state's n, u
+ * and E2:  E3_kab = u_k E2_ab + u_a E2_kb + u_b E2_ka - 2 n u_k u_a u_b
+ * (from Q = calQ - sym(u (x) calP) + 2 m n u u u with Q = 0, divided by m).
+ * The heat flux itself enters as a source (closure_source). */
+static void maxwellian_e3(const double* u, double* e3) {
+    double n = u[0];
+    if (!(n > 0.0)) {
+        for (int k = 0; k < 10; ++k) e3[k] = 0.0;
+        return;
+    }
+    double v[3] = {u[1] / n, u[2] / n, u[3] / n};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            for (int k = b; k < 3; ++k)
+                e3[sym3(a, b, k)] = v[k] * u[4 + sym2(a, b)] + v[a] * u[4 + sym2(k, b)] +
+                                    v[b] * u[4 + sym2(k, a)] - 2.0 * n * v[k] * v[a] * v[b];
+}
+
+/* temperature per mass of cell (ix, iy) (ghosts resolved like the state):
+ * theta_ab = E2_ab / n - u_a u_b */
+static void theta_at(const fl_ctx* c, const double* U, int ix, int iy, double* th) {
+    double u[10];
+    for (int k = 0; k < 10; ++k) u[k] = fetch_state(c, U, k, ix, iy);
+    double n = u[0];
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            th[sym2(a, b)] = n > 0.0 ? u[4 + sym2(a, b)] / n - (u[1 + a] / n) * (u[1 + b] / n) : 0.0;
+}
+
+/* semi-discrete right-hand side L(U); Q == NULL selects the closure model's
+ * Maxwellian third moment, reconstructed state by state */
 static void rhs(const fl_ctx* c, const double* U, const double* Q,
                 const double* EB, double* out) {
     const or_grid* g = c->g;
@@ -157,7 +192,11 @@ static void rhs(const fl_ctx* c, const double* U, const double* Q,
                     uR[k] = xl;
                     cL[k] = a1; cR[k] = a2;
                 }
-                for (int k = 0; k < nq; ++k) {
+                if (!Q) {
+                    maxwellian_e3(uL, qL);
+                    maxwellian_e3(uR, qR);
+                }
+                for (int k = 0; Q && k < nq; ++k) {
                     int ox = dir == 0, oy = dir == 1;
                     double a0 = fetch(c, Q, nq, k, lx - ox, ly - oy, 1);
                     double a1 = fetch(c, Q, nq, k, lx, ly, 1);
@@ -203,7 +242,11 @@ static void rhs(const fl_ctx* c, const double* U, const double* Q,
                     uR[k] = xl;
                     cL[k] = a1; cR[k] = a2;
                 }
-                for (int k = 0; k < nq; ++k) {
+                if (!Q) {
+                    maxwellian_e3(uL, qL);
+                    maxwellian_e3(uR, qR);
+                }
+                for (int k = 0; Q && k < nq; ++k) {
                     double a0 = fetch(c, Q, nq, k, ix, -2, 1);
                     double a1 = fetch(c, Q, nq, k, ix, -1, 1);
                     double a2 = fetch(c, Q, nq, k, ix, 0, 1);
@@ -276,3 +319,70 @@ int or_fluid_step(double* U, const or_grid* g, const or_species* sp,
     free(L); free(U1); free(U2);
     return 0;
 }
+
+/* The heat-flux closure of Sec. 2.3, Eq. (gradient closure):
+ *   div Q_s = -(chi / k_s0) n_s v_ts lap T_s,  chi = 2 sqrt(2/pi),
+ *   v_ts = sqrt(tr(T_s) / (3 m_s)), k_s0 = 1/d_s,
+ * so the second-moment equation (divided by m, T = m theta) gains the source
+ * -(1/m) div Q = (chi / k_s0) n v_t lap theta, with the five-point Laplacian
+ * of theta at cell centres (ghost cells as for the state: periodic, or the
+ * mirror cell with the parity of the component beyond a wall). */
+static void closure_source(const fl_ctx* c, const double* U, double chi_k0, double* out) {
+    const or_grid* g = c->g;
+    for (int iy = 0; iy < g->ny; ++iy)
+        for (int ix = 0; ix < g->nx; ++ix) {
+            double t0[6], txm[6], txp[6], tym[6], typ[6];
+            theta_at(c, U, ix, iy, t0);
+            theta_at(c, U, ix - 1, iy, txm);
+            theta_at(c, U, ix + 1, iy, txp);
+            theta_at(c, U, ix, iy - 1, tym);
+            theta_at(c, U, ix, iy + 1, typ);
+            long i = (long)iy * g->nx + ix;
+            double n = U[i * 10];
+            double tr = t0[0] + t0[3] + t0[5];
+            double vt = sqrt(tr > 0.0 ? tr / 3.0 : 0.0);
+            for (int k = 0; k < 6; ++k) {
+                double lap = (txp[k] - 2.0 * t0[k] + txm[k]) / (g->dx * g->dx) +
+                             (typ[k] - 2.0 * t0[k] + tym[k]) / (g->dy * g->dy);
+                out[i * 10 + 4 + k] += chi_k0 * n * vt * lap;
+            }
+        }
+}
+
+int or_fluid_step_closure(double* U, const or_grid* g, const or_species* sp,
+                          const double* EB, double dt, double chi_k0) {
+    if (g->nvdim != 3) return -1;
+    fl_ctx c;
+    c.g = g; c.sp = sp;
+    c.ncomp = 10;
+    c.nq = 10;
+    long n = (long)g->nx * g->ny * c.ncomp;
+    double* L = (double*)malloc(sizeof(double) * (size_t)n);
+    double* U1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* U2 = (double*)malloc(sizeof(double) * (size_t)n);
+    rhs(&c, U, NULL, EB, L);
+    closure_source(&c, U, chi_k0, L);
+    for (long i = 0; i < n; ++i) U1[i] = U[i] + dt * L[i];
+    rhs(&c, U1, NULL, EB, L);
+    closure_source(&c, U1, chi_k0, L);
+    for (long i = 0; i < n; ++i) U2[i] = 0.75 * U[i] + 0.25 * (U1[i] + dt * L[i]);
+    rhs(&c, U2, NULL, EB, L);
+    closure_source(&c, U2, chi_k0, L);
+    for (long i = 0; i < n; ++i) U[i] = U[i] / 3.0 + 2.0 / 3.0 * (U2[i] + dt * L[i]);
+    free(L); free(U1); free(U2);
+    return 0;
+}
+
+int or_fluid_rhs_closure(const double* U, const or_grid* g, const or_species* sp,
+                         const double* EB, double chi_k0, double* out) {
+    if (g->nvdim != 3) return -1;
+    fl_ctx c;
+    c.g = g; c.sp = sp;
+    c.ncomp = 10;
+    c.nq = 10;
+    rhs(&c, U, NULL, EB, out);
+    closure_source(&c, U, chi_k0, out);
+    return 0;
+}
+
+void or_maxwellian_e3(const double* u, double* e3) { maxwellian_e3(u, e3); }

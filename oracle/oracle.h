@@ -96,6 +96,17 @@ int or_moment_fit(double* f, const or_grid* g, const or_species* sp,
 int or_fluid_step(double* U, const or_grid* g, const or_species* sp,
                   const double* Q0, const double* Qh, const double* Q1,
                   const double* EB, double dt);
+/* The stand-alone fluid model with the gradient heat-flux closure (Sec. 2.3):
+ * the third moment in the flux is that of the state's Maxwellian, and the
+ * heat flux enters as chi_k0 n v_t lap(theta) in the second-moment equation
+ * (chi_k0 = chi / k_s0). 2D3V only. One SSP-RK3 step with EB frozen; the
+ * right-hand side alone (out[ncell][10]) for tests. */
+int or_fluid_step_closure(double* U, const or_grid* g, const or_species* sp,
+                          const double* EB, double dt, double chi_k0);
+int or_fluid_rhs_closure(const double* U, const or_grid* g, const or_species* sp,
+                         const double* EB, double chi_k0, double* out);
+/* E3 of the closure model for one state (n, nu_a, E2_ab) -> [10] */
+void or_maxwellian_e3(const double* u, double* e3);
 
 /* ---- Fields ------------------------------------------------------------- */
 /* Yee fields, one array of 6 planes, each [ny+1][nx]:

@@ -21,8 +21,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (Grid, advect_space, advect_velocity, fields_to_centres, fluid_step, make_grid,
-               make_species, maxwell, moment_fit, moments, poisson_1d)
+from . import (Grid, advect_space, advect_velocity, closure_chi_k0, fields_to_centres, fluid_step,
+               fluid_step_closure, make_grid, make_species, maxwell, moment_fit, moments, poisson_1d)
 
 
 def grid_of(cfg) -> Grid:
@@ -145,3 +145,57 @@ class OracleState:
     def mass(self):
         cfg = self.cfg
         return [moments(f, self.g, s)[:, 0].sum() for f, s in zip(self.f, self.sps)]
+
+
+class OracleClosureFluid:
+    """The stand-alone ten-moment fluid with the gradient heat-flux closure
+    (Sec. 2.3) coupled to the FDTD fields: per step a field half step with
+    the current of the fluid state, one SSP-RK3 fluid step with E and B
+    frozen, and a second field half step (the order of Algorithm 1 without
+    the kinetic part). 2D3V."""
+
+    def __init__(self, cfg, fluid_list, yee, chi_scale=1.0):
+        self.cfg = cfg
+        self.g = grid_of(cfg)
+        self.sps = [species_of(s) for s in cfg.species]
+        self.U = [np.ascontiguousarray(u, dtype=np.float64).reshape(cfg.ncell, 10).copy() for u in fluid_list]
+        self.yee = np.ascontiguousarray(yee, dtype=np.float64).reshape(-1).copy()
+        self.EB = fields_to_centres(self.yee, self.g)
+        self.chi_k0 = [chi_scale * closure_chi_k0(sp.q, sp.m) for sp in cfg.species]
+        self.time = 0.0
+
+    def current(self):
+        J = np.zeros((self.cfg.ncell, 3))
+        for sp, U in zip(self.cfg.species, self.U):
+            J += sp.q * U[:, 1:4]
+        return J
+
+    def field_half(self, h):
+        maxwell(self.yee, self.g, self.current(), h, self.cfg.c)
+        self.EB = fields_to_centres(self.yee, self.g)
+
+    def step(self, dt):
+        self.field_half(0.5 * dt)
+        EB = self.EB.copy()
+        for U, s, ck in zip(self.U, self.sps, self.chi_k0):
+            fluid_step_closure(U, self.g, s, EB, dt, ck)
+        self.field_half(0.5 * dt)
+        self.time += dt
+
+    def energies(self):
+        """(kinetic+thermal per species = (m/2) sum tr(E2) dA, electric, magnetic)"""
+        cfg = self.cfg
+        area = cfg.dx * cfg.dy
+        kin = [0.5 * sp.m * (U[:, 4] + U[:, 7] + U[:, 9]).sum() * area for sp, U in zip(cfg.species, self.U)]
+        yee = self.yee.reshape(6, cfg.ny + 1, cfg.nx)
+        eps0 = 1.0 / cfg.c ** 2
+        rows_int = slice(0, cfg.ny + 1) if cfg.bc_y == 1 else slice(0, cfg.ny)
+        ee = 0.5 * eps0 * ((yee[0, rows_int] ** 2).sum() + (yee[1, :cfg.ny] ** 2).sum()
+                           + (yee[2, rows_int] ** 2).sum()) * area
+        eb = 0.5 * ((yee[3, :cfg.ny] ** 2).sum() + (yee[4, rows_int] ** 2).sum()
+                    + (yee[5, :cfg.ny] ** 2).sum()) * area
+        return kin, ee, eb
+
+    def total_energy(self):
+        kin, ee, eb = self.energies()
+        return sum(kin) + ee + eb

@@ -19,7 +19,7 @@ VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
             "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
-            "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
+            "fluid_step_closure", "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
             "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
             "mlp_grad"]
 MLP_NPARAM = 19520  # VL_MLP_NPARAM
@@ -88,6 +88,7 @@ def lib():
     L.moment_fit_exchange.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
     L.fluid_step.argtypes = [_vp, ctypes.c_double, _dpp, _dpp, _vp]
     L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
+    L.fluid_step_closure.argtypes = [_vp, ctypes.c_double, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.vl_reset_stats.argtypes = [_vp, _vp]
     F = ctypes.POINTER(ctypes.c_float)
@@ -168,7 +169,8 @@ def vlasov_work_bytes(desc: VlDesc) -> int:
 
 def vlasov_init(desc, f_list, fluid, yee, eb, work, work_bytes):
     ctx = ctypes.c_void_p()
-    st = lib().vlasov_init(ctypes.byref(desc), _ptr_array(f_list), ptr(fluid), ptr(yee), ptr(eb), ptr(work),
+    st = lib().vlasov_init(ctypes.byref(desc), None if f_list is None else _ptr_array(f_list), ptr(fluid), ptr(yee),
+                           ptr(eb), ptr(work),
                            work_bytes, ctypes.byref(ctx))
     _check(None, st)
     return ctx
@@ -222,6 +224,11 @@ def moment_fit_exchange(ctx, species, vmom, mom_out=None, stream=None):
 
 def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):
     _check(ctx, lib().fluid_step(ctx, dt, _ptr_array(mom_t), _ptr_array(mom_t1), stream_handle(stream)))
+
+
+def fluid_step_closure(ctx, dt, stream=None):
+    """One SSP-RK3 step of the gradient-closure fluid model (Sec. 2.3)."""
+    _check(ctx, lib().fluid_step_closure(ctx, dt, stream_handle(stream)))
 
 
 def maxwell_step(ctx, h, mom=None, stream=None):

@@ -158,6 +158,7 @@ void fill_box(const vl_desc& d, int s, double* vmin, double* dv) {
 vl_status check_species(vl_ctx* ctx, int s) {
     if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
     if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species %d out of range", s);
+    if (!ctx->f[s]) return fail(ctx, VL_EINVAL, "species %d has no distribution function (fluid-only context)", s);
     return VL_OK;
 }
 
@@ -176,9 +177,8 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     *out = nullptr;
     vl_status st = validate(desc, nullptr);
     if (st != VL_OK) return st;
-    if (!f_dev) return fail(nullptr, VL_EINVAL, "f_dev is NULL");
-    for (int s = 0; s < desc->nspecies; ++s)
-        if (!f_dev[s]) return fail(nullptr, VL_EINVAL, "f_dev[%d] is NULL", s);
+    // f_dev (or an entry) may be NULL for a fluid-only context: the calls
+    // that touch f then fail with VL_EINVAL
     if (!fluid_dev || !eb_dev) return fail(nullptr, VL_EINVAL, "fluid and eb buffers are required");
     if (desc->nvdim == 3 && !yee_dev) return fail(nullptr, VL_EINVAL, "2D3V needs the Yee field buffer");
     Layout L = layout_of(*desc);
@@ -187,7 +187,7 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     if (((uintptr_t)work_dev & 255u) != 0) return fail(nullptr, VL_EINVAL, "workspace must be 256-byte aligned");
     vl_ctx* c = new vl_ctx();
     c->d = *desc;
-    for (int s = 0; s < VL_MAX_SPECIES; ++s) c->f[s] = s < desc->nspecies ? f_dev[s] : nullptr;
+    for (int s = 0; s < VL_MAX_SPECIES; ++s) c->f[s] = (f_dev && s < desc->nspecies) ? f_dev[s] : nullptr;
     c->fluid = fluid_dev;
     c->yee = yee_dev;
     c->eb = eb_dev;
@@ -541,6 +541,49 @@ vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double
     return moment_fit_exchange(ctx, s, vmom, mom_out, stream);
 }
 
+vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    const vl_desc& d = ctx->d;
+    if (d.nvdim != 3) return fail(ctx, VL_EINVAL, "the gradient-closure fluid model is 2D3V");
+    if (!std::isfinite(dt)) return fail(ctx, VL_EINVAL, "dt is not finite");
+    const double chi = 2.0 * std::sqrt(2.0 / 3.14159265358979323846);
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (int s = 0; s < d.nspecies; ++s) {
+        double* U = ctx->fluid + (size_t)s * ncell_of(d) * 10;
+        vl::FluidArgs a;
+        a.U = U;
+        a.eb = ctx->eb;
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.bc_y = d.bc_y;
+        a.nvdim = 3;
+        a.nmom = 20;
+        a.precision = d.precision;
+        a.dx = d.dx;
+        a.dy = d.dy;
+        a.qm = d.q[s] / d.m[s];
+        a.dt = dt;
+        a.q0 = nullptr;
+        a.q1 = nullptr;
+        a.wq0 = 0.0;
+        a.wq1 = 0.0;
+        a.closure = 1;
+        // chi / k_s0 with k_s0 = 1/d_s, d_s = sqrt(m_s / (n0 q_s^2)) at n0 = 1 (mu0 = 1)
+        if (d.q[s] == 0.0) return fail(ctx, VL_EINVAL, "species %d: the closure needs a charged species", s);
+        a.chi_k0 = chi * std::sqrt(d.m[s] / (d.q[s] * d.q[s]));
+        a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.a0 = 0.0; a.a1 = 1.0;
+        vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step_closure");
+        if (e != VL_OK) return e;
+        a.Us = ctx->ws.fluid_u1; a.Uout = ctx->ws.fluid_u2; a.a0 = 0.75; a.a1 = 0.25;
+        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step_closure");
+        if (e != VL_OK) return e;
+        a.Us = ctx->ws.fluid_u2; a.Uout = U; a.a0 = 1.0 / 3.0; a.a1 = 2.0 / 3.0;
+        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step_closure");
+        if (e != VL_OK) return e;
+    }
+    return VL_OK;
+}
+
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,
                      vl_stream_t stream) {
     if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
@@ -567,6 +610,8 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
         a.dt = dt;
         a.q0 = mom_t[s];
         a.q1 = mom_t1[s];
+        a.closure = 0;
+        a.chi_k0 = 0.0;
         // stage 1: U1 = U + dt L(U; Q^t)
         a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.wq0 = 1.0; a.wq1 = 0.0; a.a0 = 0.0; a.a1 = 1.0;
         vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");

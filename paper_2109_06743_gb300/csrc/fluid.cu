@@ -1,6 +1,7 @@
 // Ten-moment fluid step (paper Sec. 2.1 equations with the third moment from
 // f, Sec. 2.2; CWENO of Kurganov and Levy 2000 and SSP-RK3 of Shu and Osher
-// 1988, cited in Sec. 2.1).
+// 1988, cited in Sec. 2.1). With FluidArgs.closure the same kernel runs the
+// stand-alone fluid model of Sec. 2.3 (gradient heat-flux closure).
 //
 // Per species the state is U = (n, nu_a, E2_ab), E2 = P/m = int v v f. The
 // equations divided by m read
@@ -131,6 +132,37 @@ __device__ __forceinline__ R flux_of(int nvdim, int dir, int k, const R* u, cons
     return q[s3(dir, ab[k - 4][0], ab[k - 4][1])];
 }
 
+// Gradient-closure model (Sec. 2.3): with zero heat flux the third moment
+// is that of the Maxwellian with the state's n, u and E2,
+//   E3_kab = u_k E2_ab + u_a E2_kb + u_b E2_ka - 2 n u_k u_a u_b,
+// evaluated on the reconstructed interface states.
+template <typename R>
+__device__ __forceinline__ void closure_e3(const R* s, R* e3) {
+    const R n = s[0];
+    if (!(n > R(0))) {
+        for (int k = 0; k < 10; ++k) e3[k] = R(0);
+        return;
+    }
+    const R inv = R(1) / n;
+    const R v[3] = {s[1] * inv, s[2] * inv, s[3] * inv};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            for (int k = b; k < 3; ++k)
+                e3[s3(a, b, k)] = v[k] * s[4 + s2(a, b)] + v[a] * s[4 + s2(k, b)] + v[b] * s[4 + s2(k, a)] -
+                                  R(2) * n * v[k] * v[a] * v[b];
+}
+
+// theta = E2 / n - u u of cell (ix, iy), ghosts as for the state
+template <typename R>
+__device__ __forceinline__ void theta_cell(const FluidCtx& c, int ix, int iy, R* th) {
+    R s[10];
+    for (int k = 0; k < 10; ++k) s[k] = state_at<R>(c, k, ix, iy);
+    const R n = s[0];
+    const R inv = n > R(0) ? R(1) / n : R(0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) th[s2(a, b)] = s[4 + s2(a, b)] * inv - (s[1 + a] * inv) * (s[1 + b] * inv);
+}
+
 // numerical flux through the interface between cell (lx, ly) and its
 // neighbour in direction dir
 template <typename R>
@@ -148,7 +180,11 @@ __device__ void interface_flux(const FluidCtx& c, int dir, int lx, int ly, R* H)
         cL[k] = a1;
         cR[k] = a2;
     }
-    for (int k = 0; k < c.nq; ++k) {
+    if (c.a->closure) {
+        closure_e3<R>(uL, qL);
+        closure_e3<R>(uR, qR);
+    }
+    for (int k = 0; !c.a->closure && k < c.nq; ++k) {
         R a0 = q_at<R>(c, k, lx - ox, ly - oy), a1 = q_at<R>(c, k, lx, ly);
         R a2 = q_at<R>(c, k, lx + ox, ly + oy), a3 = q_at<R>(c, k, lx + 2 * ox, ly + 2 * oy);
         R l, r;
@@ -213,6 +249,22 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
         }
         for (int p = 0; p < 3; ++p)
             for (int q = p; q < 3; ++q) L[4 + s2(p, q)] += qm * (nu[p] * E[q] + nu[q] * E[p] + C[p][q] + C[q][p]);
+        if (a.closure) {
+            // heat flux of the closure: -(1/m) div Q = chi_k0 n v_t lap theta,
+            // v_t = sqrt(tr(theta) / 3), five-point Laplacian
+            R t0[6], tw[6], te[6], ts[6], tn[6];
+            theta_cell<R>(c, ix, iy, t0);
+            theta_cell<R>(c, ix - 1, iy, tw);
+            theta_cell<R>(c, ix + 1, iy, te);
+            theta_cell<R>(c, ix, iy - 1, ts);
+            theta_cell<R>(c, ix, iy + 1, tn);
+            const R tr = t0[0] + t0[3] + t0[5];
+            const R vt = sqrt(tr > R(0) ? tr / R(3) : R(0));
+            const R coef = (R)a.chi_k0 * u[0] * vt;
+            const R ix2 = (R)(1.0 / (a.dx * a.dx)), iy2 = (R)(1.0 / (a.dy * a.dy));
+            for (int k = 0; k < 6; ++k)
+                L[4 + k] += coef * ((te[k] - R(2) * t0[k] + tw[k]) * ix2 + (tn[k] - R(2) * t0[k] + ts[k]) * iy2);
+        }
     }
     for (int k = 0; k < c.nc; ++k) {
         double us = a.Us[cell * c.nc + k];

@@ -188,6 +188,9 @@ struct FluidArgs {
     int precision;          // 64: right-hand side in FP64; 32: in FP32 (state FP64)
     double dx, dy, qm, dt;
     double a0, a1;          // Uout = a0 * U0 + a1 * (Us + dt L(Us))
+    int closure;            // 1: gradient-closure model (third moment of the state's
+                            // Maxwellian, heat flux as chi_k0 n v_t lap theta); q0, q1 unused
+    double chi_k0;          // chi / k_s0 of the closure
 };
 cudaError_t launch_fluid_stage(const FluidArgs& a, cudaStream_t st);
 

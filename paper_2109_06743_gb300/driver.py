@@ -173,3 +173,69 @@ class Simulation:
     def total_energy(self):
         kin, ee, eb = self.energies()
         return sum(kin) + ee + eb
+
+
+class ClosureFluid:
+    """The stand-alone ten-moment fluid model with the gradient heat-flux
+    closure (Sec. 2.3) through the C-ABI, on a fluid-only context (no f):
+    per step maxwell_step(dt/2) with the current of the fluid state,
+    fluid_step_closure(dt), maxwell_step(dt/2). 2D3V."""
+
+    def __init__(self, cfg, fluid_list, yee, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.cfg = cfg
+        self.dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        nc = cfg.ncell
+        with torch.cuda.stream(self.stream):
+            self.fluid = torch.as_tensor(np.stack([np.asarray(u, dtype=np.float64).reshape(nc, 10)
+                                                   for u in fluid_list])).to(self.dev).contiguous()
+            self.eb = torch.zeros((nc, 6), dtype=torch.float64, device=self.dev)
+            self.yee = torch.as_tensor(np.asarray(yee, dtype=np.float64).reshape(-1)).to(self.dev).contiguous()
+            self.desc = abi.make_desc(cfg)
+            self.work_bytes = abi.vlasov_work_bytes(self.desc)
+            if self.work_bytes == 0:
+                raise abi.VlasovError(abi.VL_EINVAL, abi.lib().vl_last_error(None).decode())
+            self.work = torch.zeros(self.work_bytes + 256, dtype=torch.uint8, device=self.dev)
+            self.work_ptr = self.work.data_ptr() + (-self.work.data_ptr()) % 256
+        self.ctx = abi.vlasov_init(self.desc, None, self.fluid, self.yee, self.eb, self.work_ptr, self.work_bytes)
+        abi.maxwell_step(self.ctx, 0.0, None, self.stream)  # cell-centred fields
+        self.time = 0.0
+
+    def step(self, dt=None):
+        dt = self.cfg.dt if dt is None else dt
+        abi.maxwell_step(self.ctx, 0.5 * dt, None, self.stream)
+        abi.fluid_step_closure(self.ctx, dt, self.stream)
+        abi.maxwell_step(self.ctx, 0.5 * dt, None, self.stream)
+        self.time += dt
+
+    def energies(self):
+        """(kinetic+thermal per species = (m/2) sum tr(E2) dA, electric, magnetic)"""
+        cfg = self.cfg
+        self.stream.synchronize()
+        area = cfg.dx * cfg.dy
+        U = self.fluid.cpu().numpy()
+        kin = [0.5 * sp.m * (U[k, :, 4] + U[k, :, 7] + U[k, :, 9]).sum() * area for k, sp in enumerate(cfg.species)]
+        y = self.yee.cpu().numpy().reshape(6, cfg.ny + 1, cfg.nx)
+        rows = slice(0, cfg.ny + 1) if cfg.bc_y == 1 else slice(0, cfg.ny)
+        eps0 = 1.0 / cfg.c ** 2
+        ee = 0.5 * eps0 * ((y[0, rows] ** 2).sum() + (y[1, :cfg.ny] ** 2).sum() + (y[2, rows] ** 2).sum()) * area
+        eb = 0.5 * ((y[3, :cfg.ny] ** 2).sum() + (y[4, rows] ** 2).sum() + (y[5, :cfg.ny] ** 2).sum()) * area
+        return kin, ee, eb
+
+    def total_energy(self):
+        kin, ee, eb = self.energies()
+        return sum(kin) + ee + eb
+
+    def close(self):
+        if self.ctx is not None:
+            abi.vlasov_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -397,3 +397,84 @@ def wave2d_yee(cfg: Config):
     yee = np.zeros((6, cfg.ny + 1, cfg.nx))
     yee[5, :cfg.ny, :] = cfg.bz
     return yee
+
+
+# ------------------------------------------------------------- Orszag-Tang ---
+
+def orszag_tang(n=64, L=25.6, mass_ratio=100.0, beta_i=0.1, ti_te=1.0, du=0.2, dB=0.2, c=18.174, nv=8,
+                steps=200, precision=64) -> Config:
+    """Orszag-Tang turbulence of Sec. 3.2 (initial conditions of the cited
+    PIC study, parameters A1) on an n x n periodic grid of side L (d_i = 1,
+    B0 = n0 = v_A = 1): m_i/m_e = 100, T_i = T_e from beta_i = 2 n0 T_i / B0^2
+    = 0.1, c = 18.174 v_A, delta_u = delta_B = 0.2. At the paper's 512^2 the
+    box is L = 25.6 d_i (two cells per d_e); a smaller n keeps L and
+    coarsens the grid. nv only sizes the velocity boxes (+-5 v_th) of a
+    kinetic run of the same set-up."""
+    ti = 0.5 * beta_i
+    te = ti / ti_te
+    species = []
+    for name, q, m, t in (("e", -1.0, 1.0 / mass_ratio, te), ("i", 1.0, 1.0, ti)):
+        vm = 5.0 * math.sqrt(t / m) + du
+        sp = SpeciesCfg(name, q, m, (nv, nv, nv), (-vm, -vm, -vm), (vm, vm, vm))
+        sp.T = t
+        species.append(sp)
+    dx = L / n
+    # the explicit coupling of the fluid current and the fields must resolve
+    # the electron plasma and cyclotron oscillations (omega_pe = c sqrt(n0/m_e)
+    # = 182 at these parameters, omega_ce = 100 B), besides the light CFL
+    w_pe = c * math.sqrt(mass_ratio)
+    dt = min(0.5 * dx / c, 0.2 / w_pe, 0.2 / (mass_ratio * 1.5))
+    cfg = Config("orszag_tang_%d" % n, 3, n, n, 0.0, L, 0.0, L, 0, species, dt, steps, c=c,
+                 precision=precision)
+    cfg.du, cfg.dB, cfg.kind = du, dB, "orszag_tang"
+    return cfg
+
+
+def _ot_Az(cfg, x, y):
+    # B = curl(A_z z): B_x = dA/dy = -dB sin(2 pi y/L), B_y = -dA/dx = dB sin(4 pi x/L)
+    L = cfg.lx
+    return cfg.dB * (L / (2 * math.pi)) * np.cos(2 * math.pi * y / L) + cfg.dB * (L / (4 * math.pi)) * np.cos(
+        4 * math.pi * x / L)
+
+
+def orszag_tang_yee(cfg: Config):
+    """Yee fields: B from A_z plus B_z = 1; E from ideal Ohm's law,
+    E_x = -du sin(2 pi x/L) at (i+1/2, j), E_y = -du sin(2 pi y/L) at (i, j+1/2)."""
+    yee = yee_from_Az(cfg, _ot_Az, bz=1.0)
+    k = 2 * math.pi / cfg.lx
+    xh = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    yh = cfg.y0 + (np.arange(cfg.ny) + 0.5) * cfg.dy
+    yee[0, :, :] = -cfg.du * np.sin(k * xh)[None, :]
+    yee[1, :cfg.ny, :] = -cfg.du * np.sin(k * yh)[:, None]
+    return yee
+
+
+def orszag_tang_fluid(cfg: Config):
+    """(n, nu, int v v f) per species at the cell centres: uniform density
+    (electrons perturbed so that Gauss's law holds for the initial E),
+    u_x = -du sin(2 pi y/L), u_y = du sin(2 pi x/L), u_z,i = 0 and u_z,e
+    carrying the current j_z = dB_y/dx - dB_x/dy, isotropic temperatures."""
+    L = cfg.lx
+    x = cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx
+    y = cfg.y0 + (np.arange(cfg.ny) + 0.5) * cfg.dy
+    X, Y = np.meshgrid(x, y)
+    k = 2 * math.pi / L
+    divE = -cfg.du * k * (np.cos(k * X) + np.cos(k * Y))
+    jz = cfg.dB * 2 * k * np.cos(2 * k * X) + cfg.dB * k * np.cos(k * Y)
+    out = []
+    for sp in cfg.species:
+        n = np.ones_like(X) if sp.q > 0 else 1.0 - divE / cfg.c ** 2
+        ux, uy = -cfg.du * np.sin(k * Y), cfg.du * np.sin(k * X)
+        uz = np.zeros_like(X) if sp.q > 0 else jz / (sp.q * n)
+        th = sp.T / sp.m
+        U = np.zeros((cfg.ny, cfg.nx, 10))
+        U[..., 0] = n
+        U[..., 1], U[..., 2], U[..., 3] = n * ux, n * uy, n * uz
+        U[..., 4] = n * (th + ux * ux)
+        U[..., 5] = n * ux * uy
+        U[..., 6] = n * ux * uz
+        U[..., 7] = n * (th + uy * uy)
+        U[..., 8] = n * uy * uz
+        U[..., 9] = n * (th + uz * uz)
+        out.append(U.reshape(cfg.ncell, 10))
+    return out
