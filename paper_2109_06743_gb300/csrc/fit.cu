@@ -186,10 +186,15 @@ __device__ __forceinline__ void add_maxwellian(float (&r)[N], const float* pd, i
 // m = k - k0, delta = kc - k0, C = exp(Ec - hz delta^2), A = exp(2 hz delta)
 // and the per-cell table G(m) = exp(-hz m^2); three exponentials per line.
 // The factors stay in range for hz <= 8 (sigma above a quarter cell);
-// narrower Maxwellians take one exponential per element.
+// narrower Maxwellians take one exponential per element. Not inlined: with
+// the line in registers and inlined twice into exchange_kernel<double, 20>,
+// the optimised build gave wrong values (checked against a direct
+// evaluation; the same code called out of line, every other block size and
+// every optimisation level below -O2 agree with it), so the FP64 line update
+// is a call.
 template <int N>
-__device__ __forceinline__ void add_maxwellian(double (&r)[N], const double* pd, int i, int j, double sgn,
-                                               const double* G) {
+__device__ __noinline__ void add_maxwellian(double (&r)[N], const double* pd, int i, int j, double sgn,
+                                            const double* G) {
     const double hz = pd[8];
     if (!(hz > 0.0)) return;
     const double dx = i - pd[0], dy = j - pd[1];

@@ -232,11 +232,13 @@ def fluid_targets(cfg, orc, f_list, seed):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-def test_moment_fit_matches_oracle(gpu, orc, precision):
+@pytest.mark.parametrize("nv", [12, 8, 16, 20, 24])
+def test_moment_fit_matches_oracle(gpu, orc, precision, nv):
     from gpu_util import AbiRunner
     from paper_2109_06743_gb300 import abi
-    cfg = small_harris(nx=6, ny=6, nv=12, precision=precision)
-    cfg.fit_tol = 1e-12
+    cfg = small_harris(nx=6, ny=6 if nv <= 16 else 3, nv=nv, precision=precision)
+    # double-float sums over 20^3 and 24^3 cells reach 1e-11 n, not 1e-12 n
+    cfg.fit_tol = 1e-12 if nv <= 16 else 1e-11
     f0 = [cast(f, precision) for f in near_maxwellian_state(cfg, 400)]
     U0 = fluid_targets(cfg, orc, f0, 401)
     r = AbiRunner(cfg, f0, fluid=np.stack(U0))
@@ -265,8 +267,10 @@ def test_moment_fit_matches_oracle(gpu, orc, precision):
             if stt == 0:
                 np.testing.assert_allclose(thv[c].cpu().numpy(), th, rtol=1e-8, atol=1e-12 * abs(th).max())
         # moments after the exchange equal the (rescaled) fluid targets when nothing was clipped
+        # fits that do not converge fall back to the continuous Maxwellian on
+        # both sides (8^3 ions: targets that no discrete Maxwellian matches)
         stats = abi.vl_read_stats(r.ctx)
-        assert stats[1] == 0 and stats[3] == 0, stats
+        assert stats[1] == st[1] and stats[3] == 0, (stats, st)
         if st[2] == 0:
             m_after = mout.cpu().numpy()
             dv = sp.dv[0]
