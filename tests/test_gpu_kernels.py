@@ -129,11 +129,11 @@ def test_fused_xy_sweep(gpu, orc, precision, bc_y, cfl, grid):
 
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("nshear", [5, 3])
-@pytest.mark.parametrize("nv", [8, 12])
+@pytest.mark.parametrize("nv", [8, 12, 16, 20, 24])
 def test_velocity_pass_and_fused_moments(gpu, orc, precision, nshear, nv):
     from gpu_util import AbiRunner
     from paper_2109_06743_gb300 import abi
-    cfg = small_harris(nx=5, ny=4, nv=nv, precision=precision)
+    cfg = small_harris(nx=5, ny=4 if nv <= 12 else 3, nv=nv, precision=precision)
     cfg.nshear = nshear
     V = nv ** 3
     f0 = [cast(W.random_blocks((cfg.ncell, V), 200 + k) ** 4, precision) for k in range(2)]
