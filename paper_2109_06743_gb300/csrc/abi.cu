@@ -72,7 +72,7 @@ long long vblock_of(const vl_desc& d, int s) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, counters;
+    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, fluid_f, counters;
     size_t mlp_w, mlp_m, mlp_v, mlp_g, mlp_acc, mlp_err, mlp_pred, harvest_count, total;
 };
 
@@ -87,6 +87,7 @@ Layout layout_of(const vl_desc& d) {
     L.u1 = off; off = align256(off + nc * 10 * sizeof(double));
     L.u2 = off; off = align256(off + nc * 10 * sizeof(double));
     L.cur = off; off = align256(off + nc * 3 * sizeof(double));
+    L.fluid_f = off; off = align256(off + 2 * nc * 10 * sizeof(float));
     L.counters = off; off = align256(off + VL_NSTATS * sizeof(unsigned long long));
     const size_t np = (size_t)VL_MLP_NPARAM * sizeof(float);
     L.mlp_w = off; off = align256(off + np);
@@ -200,6 +201,7 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     c->ws.fluid_u2 = reinterpret_cast<double*>(w + L.u2);
     c->ws.fluid_l = nullptr;
     c->ws.cur = reinterpret_cast<double*>(w + L.cur);
+    c->ws.fluid_f = reinterpret_cast<float*>(w + L.fluid_f);
     c->ws.counters = reinterpret_cast<unsigned long long*>(w + L.counters);
     c->ws.mlp = nullptr;
     c->mlp_w = reinterpret_cast<float*>(w + L.mlp_w);
@@ -568,6 +570,8 @@ vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
         a.wq0 = 0.0;
         a.wq1 = 0.0;
         a.closure = 1;
+        a.Usf = ctx->ws.fluid_f;
+        a.Qf = nullptr;
         // chi / k_s0 with k_s0 = 1/d_s, d_s = sqrt(m_s / (n0 q_s^2)) at n0 = 1 (mu0 = 1)
         if (d.q[s] == 0.0) return fail(ctx, VL_EINVAL, "species %d: the closure needs a charged species", s);
         a.chi_k0 = chi * std::sqrt(d.m[s] / (d.q[s] * d.q[s]));
@@ -612,6 +616,8 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
         a.q1 = mom_t1[s];
         a.closure = 0;
         a.chi_k0 = 0.0;
+        a.Usf = ctx->ws.fluid_f;
+        a.Qf = ctx->ws.fluid_f + (size_t)ncell_of(d) * 10;
         // stage 1: U1 = U + dt L(U; Q^t)
         a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.wq0 = 1.0; a.wq1 = 0.0; a.a0 = 0.0; a.a1 = 1.0;
         vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");

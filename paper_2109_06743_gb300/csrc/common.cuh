@@ -40,6 +40,7 @@ struct Workspace {
     double* fluid_u2;     // [ncell][10]
     double* fluid_l;      // [ncell][10]
     double* cur;          // [ncell][3] current density at cell centres
+    float* fluid_f;       // [2][ncell][10] FP32 copies of a stage's state and third moments
     unsigned long long* counters;  // [VL_NSTATS]
     float* mlp;           // MLP weights and scratch
 };

@@ -92,23 +92,33 @@ __device__ __forceinline__ long long resolve(const FluidArgs& a, int ix, int iy,
     return (long long)iy * a.nx + ix;
 }
 
+// In FP32 mode the stage input and the weighted third moments are converted
+// to float once per stage (fluid_prep_kernel) instead of at each of the ~16
+// stencil reads of every value (FP64-to-FP32 conversions run on the FP64
+// pipe); the values are the same.
 template <typename R>
 __device__ __forceinline__ R state_at(const FluidCtx& c, int k, int ix, int iy) {
     bool mir;
     long long id = resolve(*c.a, ix, iy, &mir);
-    R v = (R)c.a->Us[id * c.nc + k];
+    R v = (sizeof(R) == 4 && c.a->Usf) ? (R)c.a->Usf[id * c.nc + k] : (R)c.a->Us[id * c.nc + k];
     return (mir && c.a->nvdim == 3) ? v * (R)parity_state(k) : v;
 }
 
 // Q = wq0 q0 + wq1 q1 (the weights are 0, 1/2 or 1, exact in R)
 template <typename R>
+__device__ __forceinline__ R q_value(const FluidArgs& a, const FluidCtx& c, long long id, int k) {
+    R v = R(0);
+    if (c.use0) v += (R)a.wq0 * (R)a.q0[id * a.nmom + c.qoff + k];
+    if (c.use1) v += (R)a.wq1 * (R)a.q1[id * a.nmom + c.qoff + k];
+    return v;
+}
+
+template <typename R>
 __device__ __forceinline__ R q_at(const FluidCtx& c, int k, int ix, int iy) {
     bool mir;
     long long id = resolve(*c.a, ix, iy, &mir);
     const FluidArgs& a = *c.a;
-    R v = R(0);
-    if (c.use0) v += (R)a.wq0 * (R)a.q0[id * a.nmom + c.qoff + k];
-    if (c.use1) v += (R)a.wq1 * (R)a.q1[id * a.nmom + c.qoff + k];
+    const R v = (sizeof(R) == 4 && a.Qf) ? (R)a.Qf[id * c.nq + k] : q_value<R>(a, c, id, k);
     return (mir && a.nvdim == 3) ? v * (R)parity_q(k) : v;
 }
 
@@ -163,41 +173,80 @@ __device__ __forceinline__ void theta_cell(const FluidCtx& c, int ix, int iy, R*
         for (int b = a; b < 3; ++b) th[s2(a, b)] = s[4 + s2(a, b)] * inv - (s[1 + a] * inv) * (s[1 + b] * inv);
 }
 
-// numerical flux through the interface between cell (lx, ly) and its
-// neighbour in direction dir
+// value of component k of the state (q = false) or of the third moments
+// (q = true) in a resolved cell (id, mirror flag)
 template <typename R>
-__device__ void interface_flux(const FluidCtx& c, int dir, int lx, int ly, R* H) {
-    const int ox = dir == 0, oy = dir == 1;
-    R uL[10], uR[10], cL[10], cR[10], qL[10], qR[10];
+__device__ __forceinline__ R value_at(const FluidCtx& c, bool q, int k, long long id, bool mir) {
+    const FluidArgs& a = *c.a;
+    R v;
+    if (!q) v = (sizeof(R) == 4 && a.Usf) ? (R)a.Usf[id * c.nc + k] : (R)a.Us[id * c.nc + k];
+    else v = (sizeof(R) == 4 && a.Qf) ? (R)a.Qf[id * c.nq + k] : q_value<R>(a, c, id, k);
+    if (mir && a.nvdim == 3) v *= (R)(q ? parity_q(k) : parity_state(k));
+    return v;
+}
+
+// Numerical fluxes through the two interfaces of a cell in direction dir
+// (Hm: with the neighbour below, Hp: with the neighbour above). The five
+// cells of the stencil are resolved once; each of the three middle cells is
+// reconstructed once (its left and right interface values), which serves
+// both interfaces.
+template <typename R>
+__device__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R* Hp) {
+    long long id[5];
+    bool mir[5];
+    for (int o = 0; o < 5; ++o)
+        id[o] = resolve(*c.a, ix + (dir == 0 ? o - 2 : 0), iy + (dir == 1 ? o - 2 : 0), &mir[o]);
+    // uE[p][side]: reconstruction in cell p-1 (p = 0, 1, 2 for cells -1, 0, +1)
+    R um[10], u0[10], up[10], cm[10], c0[10], cp[10];  // left/right states of the two interfaces
+    R qm_[10], q0_[10], qp_[10], qmm[10];
     for (int k = 0; k < c.nc; ++k) {
-        R a0 = state_at<R>(c, k, lx - ox, ly - oy), a1 = state_at<R>(c, k, lx, ly);
-        R a2 = state_at<R>(c, k, lx + ox, ly + oy), a3 = state_at<R>(c, k, lx + 2 * ox, ly + 2 * oy);
+        const R a0 = value_at<R>(c, false, k, id[0], mir[0]), a1 = value_at<R>(c, false, k, id[1], mir[1]);
+        const R a2 = value_at<R>(c, false, k, id[2], mir[2]), a3 = value_at<R>(c, false, k, id[3], mir[3]);
+        const R a4 = value_at<R>(c, false, k, id[4], mir[4]);
         R l, r;
-        cweno3_point<R>(a0, a1, a2, &l, &r);
-        uL[k] = r;
-        cweno3_point<R>(a1, a2, a3, &l, &r);
-        uR[k] = l;
-        cL[k] = a1;
-        cR[k] = a2;
+        cweno3_point<R>(a0, a1, a2, &l, &r);  // cell -1
+        um[k] = r;                            // left state of the lower interface
+        cweno3_point<R>(a1, a2, a3, &l, &r);  // cell 0
+        u0[k] = l;                            // right state of the lower interface
+        up[k] = r;                            // left state of the upper interface
+        cweno3_point<R>(a2, a3, a4, &l, &r);  // cell +1
+        cp[k] = l;                            // right state of the upper interface
+        cm[k] = a1;
+        c0[k] = a2;
+        qmm[k] = a3;  // cell averages of cell +1 (wave speed)
     }
     if (c.a->closure) {
-        closure_e3<R>(uL, qL);
-        closure_e3<R>(uR, qR);
+        closure_e3<R>(um, qm_);
+        closure_e3<R>(u0, q0_);
+        closure_e3<R>(up, qp_);
     }
-    for (int k = 0; !c.a->closure && k < c.nq; ++k) {
-        R a0 = q_at<R>(c, k, lx - ox, ly - oy), a1 = q_at<R>(c, k, lx, ly);
-        R a2 = q_at<R>(c, k, lx + ox, ly + oy), a3 = q_at<R>(c, k, lx + 2 * ox, ly + 2 * oy);
-        R l, r;
-        cweno3_point<R>(a0, a1, a2, &l, &r);
-        qL[k] = r;
-        cweno3_point<R>(a1, a2, a3, &l, &r);
-        qR[k] = l;
+    R qcp[10];
+    if (c.a->closure) {
+        closure_e3<R>(cp, qcp);
+    } else {
+        for (int k = 0; k < c.nq; ++k) {
+            const R a0 = value_at<R>(c, true, k, id[0], mir[0]), a1 = value_at<R>(c, true, k, id[1], mir[1]);
+            const R a2 = value_at<R>(c, true, k, id[2], mir[2]), a3 = value_at<R>(c, true, k, id[3], mir[3]);
+            const R a4 = value_at<R>(c, true, k, id[4], mir[4]);
+            R l, r;
+            cweno3_point<R>(a0, a1, a2, &l, &r);
+            qm_[k] = r;
+            cweno3_point<R>(a1, a2, a3, &l, &r);
+            q0_[k] = l;
+            qp_[k] = r;
+            cweno3_point<R>(a2, a3, a4, &l, &r);
+            qcp[k] = l;
+        }
     }
     const int nvdim = c.a->nvdim;
-    R sp = fmax(wave_speed<R>(nvdim, dir, cL), wave_speed<R>(nvdim, dir, cR));
-    for (int k = 0; k < c.nc; ++k)
-        H[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, uL, qL) + flux_of<R>(nvdim, dir, k, uR, qR)) -
-               R(0.5) * sp * (uR[k] - uL[k]);
+    const R sm = fmax(wave_speed<R>(nvdim, dir, cm), wave_speed<R>(nvdim, dir, c0));
+    const R sp = fmax(wave_speed<R>(nvdim, dir, c0), wave_speed<R>(nvdim, dir, qmm));
+    for (int k = 0; k < c.nc; ++k) {
+        Hm[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, um, qm_) + flux_of<R>(nvdim, dir, k, u0, q0_)) -
+                R(0.5) * sm * (u0[k] - um[k]);
+        Hp[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, up, qp_) + flux_of<R>(nvdim, dir, k, cp, qcp)) -
+                R(0.5) * sp * (cp[k] - up[k]);
+    }
 }
 
 template <typename R>
@@ -218,8 +267,7 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
     R Hm[10], Hp[10];
     for (int dir = 0; dir < ndir; ++dir) {
         const R invh = (R)(1.0 / (dir == 0 ? a.dx : a.dy));
-        interface_flux<R>(c, dir, ix - (dir == 0), iy - (dir == 1), Hm);
-        interface_flux<R>(c, dir, ix, iy, Hp);
+        cell_fluxes<R>(c, dir, ix, iy, Hm, Hp);
         // walls: the interface beyond the last row is the wall itself
         // (mirror ghosts already give its flux); nothing special needed
         for (int k = 0; k < c.nc; ++k) L[k] -= (Hp[k] - Hm[k]) * invh;
@@ -273,9 +321,34 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
     }
 }
 
-cudaError_t launch_fluid_stage(const FluidArgs& a, cudaStream_t st) {
+// FP32 copies of the stage input and of the weighted third moments
+__global__ void fluid_prep_kernel(FluidArgs a) {
+    long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= (long long)a.nx * a.ny) return;
+    FluidCtx c;
+    c.a = &a;
+    c.nc = a.nvdim == 1 ? 3 : 10;
+    c.nq = a.nvdim == 1 ? 1 : 10;
+    c.qoff = a.nvdim == 1 ? 3 : 10;
+    c.use0 = a.wq0 != 0.0;
+    c.use1 = a.wq1 != 0.0;
+    for (int k = 0; k < c.nc; ++k) a.Usf[cell * c.nc + k] = (float)a.Us[cell * c.nc + k];
+    if (a.Qf)
+        for (int k = 0; k < c.nq; ++k) a.Qf[cell * c.nq + k] = q_value<float>(a, c, cell, k);
+}
+
+cudaError_t launch_fluid_stage(const FluidArgs& args, cudaStream_t st) {
+    FluidArgs a = args;
     long long n = (long long)a.nx * a.ny;
     int threads = 128;
+    if (a.precision == 64) {
+        a.Usf = nullptr;
+        a.Qf = nullptr;
+    }
+    if (a.Usf) {
+        fluid_prep_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+        count_launch();
+    }
     if (a.precision == 64) fluid_stage_kernel<double><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
     else fluid_stage_kernel<float><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
     count_launch();

@@ -188,6 +188,8 @@ struct FluidArgs {
     int precision;          // 64: right-hand side in FP64; 32: in FP32 (state FP64)
     double dx, dy, qm, dt;
     double a0, a1;          // Uout = a0 * U0 + a1 * (Us + dt L(Us))
+    float* Usf;             // FP32 mode: [ncell][10] stage input converted once (or null)
+    float* Qf;              // FP32 mode: [ncell][10] weighted third moments (or null)
     int closure;            // 1: gradient-closure model (third moment of the state's
                             // Maxwellian, heat flux as chi_k0 n v_t lap theta); q0, q1 unused
     double chi_k0;          // chi / k_s0 of the closure
