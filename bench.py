@@ -127,15 +127,15 @@ class ClockSampler:
 # velocity cell of one evaluation in the double-float Newton fit: moments of
 # degree <= 2 (two double-float products for the recurrence, three
 # compensated accumulations, the index step), plus the FP32 sums of degree
-# <= 4 when the Jacobian is formed in the same pass. Derived operation by
-# operation in the design doc.
+# <= 4 when the Jacobian is formed in the same pass, counted operation by
+# operation.
 OPS_MOMENT_EVAL = 46
 OPS_GRAM_EVAL = 7
-# DRAM bytes per fitted cell (both fits) of newton_kernel, from the ncu
-# capture summarised in profiles/newton_kernel_harris_128x64_v16.md
-# (7.1 MB read + 14.3 MB written for 8192 cells; mostly the kernel's local
-# memory, i.e. register spills); None once the kernel has changed since.
-NEWTON_DRAM_BYTES_PER_CELL = None
+# DRAM bytes per cell of one fit launch (one species) from the ncu capture of
+# newton_kernel<16> on the 256 x 128 x 16^3 case with the warm start
+# (11.66 MB read + 19.85 MB written for 32768 cells: targets, coefficients,
+# status and the kernel's local memory); None once the kernel has changed.
+NEWTON_DRAM_BYTES_PER_CELL = (11.66e6 + 19.85e6) / 32768
 
 
 def alu_peak_tops():

@@ -12,7 +12,7 @@ Algorithm 1 (Sec. 2.2), as implemented here:
   7. moment fitting (Newton fits of the V and F Maxwellians, exchange, limit),
   8. second field half step with the current of the fitted moments.
 
-Readings where the paper is silent (listed in the design doc): Lie splitting x, y, v
+Readings where the paper is silent: Lie splitting x, y, v
 for 2D3V and Strang splitting x/2, v, x/2 for 1D1V; the fluid state is replaced
 by its rescaled moments after fitting; E in 1D1V from the density of f after
 the first half x-sweep.
