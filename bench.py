@@ -467,13 +467,11 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         ksteps = max(1, min(args.steps, 5))
         e0.record(stream)
+        sim.host_streams_after(e0)
         with torch.cuda.stream(stream):
             for _ in range(ksteps):
-                for h, f in zip(host, sim.f):
-                    f.copy_(h, non_blocking=True)
-                sim.step(use_mlp=use_mlp)
-                for h, f in zip(host, sim.f):
-                    h.copy_(f, non_blocking=True)
+                sim.step_through_host(host, use_mlp=use_mlp)
+            sim.wait_host()
         e1.record(stream)
         barrier_sync()
         et = slowest(e0.elapsed_time(e1) / 1e3, dist, device)

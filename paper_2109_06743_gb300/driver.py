@@ -91,17 +91,23 @@ class Simulation:
             pass
 
     # -- Algorithm 1 -----------------------------------------------------------
-    def step(self, dt=None, use_mlp=False, mark=None):
+    def step(self, dt=None, use_mlp=False, mark=None, first_use=None, last_use=None):
         """One time step. ``mark(label)``, if given, is called before each
-        phase (the benchmark records a CUDA event there); it does not change
-        the work."""
+        phase (the benchmark records a CUDA event there); ``first_use(k)`` and
+        ``last_use(k)``, if given, are called right before the first and
+        right after the last kernel of the step that touches f of species k
+        (step_through_host hangs its copies there). None of them changes the
+        work."""
         cfg, ctx, s = self.cfg, self.ctx, self.stream
         dt = cfg.dt if dt is None else dt
         ns = len(cfg.species)
         mark = mark or (lambda label: None)
+        first_use = first_use or (lambda k: None)
+        last_use = last_use or (lambda k: None)
         if cfg.nvdim == 1:
             abi.maxwell_step(ctx, 0.5 * dt, self.mom_t, s)
             for k in range(ns):
+                first_use(k)
                 abi.pfc_advect_x(ctx, k, 0, 0.5 * dt, s)
                 abi.moments(ctx, k, self.mom_tmp[k], s)
             abi.maxwell_step(ctx, 0.5 * dt, self.mom_tmp, s)
@@ -109,10 +115,13 @@ class Simulation:
                 abi.pfc_advect_v(ctx, k, dt, None, s)
                 abi.pfc_advect_x(ctx, k, 0, 0.5 * dt, s)
                 abi.moments(ctx, k, self.mom_t1[k], s)
+                if not self.fit:
+                    last_use(k)
         else:
             mark("maxwell")
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
             for k in range(ns):
+                first_use(k)
                 if self.fused_xy:
                     mark("xy_sweep")
                     abi.pfc_advect_xy(ctx, k, dt, self.f_spare[k], s)
@@ -124,6 +133,8 @@ class Simulation:
                     abi.pfc_advect_x(ctx, k, 1, dt, s)
                 mark("v_pass")
                 abi.pfc_advect_v(ctx, k, dt, self.mom_t1[k], s)
+                if not self.fit:
+                    last_use(k)
         if self.fit:
             mark("fluid")
             abi.fluid_step(ctx, dt, self.mom_t, self.mom_t1, s)
@@ -132,6 +143,7 @@ class Simulation:
                 abi.moment_fit_solve(ctx, k, self.mom_t1[k], use_mlp, None, None, s)
                 mark("fit_exchange")
                 abi.moment_fit_exchange(ctx, k, self.mom_t1[k], self.mom_t[k], s)
+                last_use(k)
         else:
             self.mom_t, self.mom_t1 = self.mom_t1, self.mom_t
         mark("maxwell")
@@ -141,6 +153,73 @@ class Simulation:
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
         mark(None)
         self.time += dt
+
+    # pieces per species of the host copies: the copy in of piece c of the
+    # next step follows the copy out of piece c of this one, so the two
+    # directions pipeline
+    HOST_CHUNKS = 8
+
+    def step_through_host(self, host, use_mlp=False):
+        """One step whose f comes from, and goes back to, pinned host buffers
+        host[k] (the end-to-end form). The copy of species k into the device
+        runs on its own stream and is awaited right before the species' first
+        kernel; its copy back starts as soon as the species' last kernel has
+        finished, on another stream; and the next step's copy in waits for it.
+        So one species' transfers overlap the other species' kernels, and the
+        two directions overlap each other."""
+        torch = self.torch
+        ns = len(self.cfg.species)
+        self.host_streams_after(None)
+        nch = self.HOST_CHUNKS
+        h2d_done = [None] * ns
+        for k in range(ns):
+            dev_parts, host_parts = self.f[k].chunk(nch), host[k].chunk(nch)
+            with torch.cuda.stream(self._h2d):
+                for c in range(len(dev_parts)):
+                    # chunk c of the previous step's copy back must have left
+                    if self._d2h_done[k] is not None:
+                        self._h2d.wait_event(self._d2h_done[k][c])
+                    dev_parts[c].copy_(host_parts[c], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self._h2d)
+                h2d_done[k] = ev
+
+        def first_use(k):
+            self.stream.wait_event(h2d_done[k])
+
+        def last_use(k):
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            dev_parts, host_parts = self.f[k].chunk(nch), host[k].chunk(nch)
+            done = []
+            with torch.cuda.stream(self._d2h):
+                self._d2h.wait_event(ev)
+                for c in range(len(dev_parts)):
+                    host_parts[c].copy_(dev_parts[c], non_blocking=True)
+                    e = torch.cuda.Event()
+                    e.record(self._d2h)
+                    done.append(e)
+            self._d2h_done[k] = done
+
+        self.step(use_mlp=use_mlp, first_use=first_use, last_use=last_use)
+
+    def host_streams_after(self, event):
+        """Create the copy streams of step_through_host if needed and, given
+        an event, make them wait for it (a timer's start)."""
+        torch = self.torch
+        if getattr(self, "_h2d", None) is None:
+            self._h2d = torch.cuda.Stream(self.dev)
+            self._d2h = torch.cuda.Stream(self.dev)
+            self._d2h_done = [None] * len(self.cfg.species)
+        if event is not None:
+            self._h2d.wait_event(event)
+            self._d2h.wait_event(event)
+
+    def wait_host(self):
+        """Make the solver's stream wait for the last copies back to the host."""
+        for evs in getattr(self, "_d2h_done", None) or []:
+            for ev in evs or []:
+                self.stream.wait_event(ev)
 
     # -- host-side views (diagnostics and tests) --------------------------------
     def f_host(self, k):

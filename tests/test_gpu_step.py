@@ -123,3 +123,29 @@ def test_asymmetric_sheet_fp64_steps_match_oracle(gpu, orc):
     np.testing.assert_allclose(sim.yee.cpu().numpy(), ost.yee, rtol=0, atol=1e-10 * np.abs(ost.yee).max())
     assert sim.stats()[3] == 0
     sim.close()
+
+
+@pytest.mark.parametrize("fit", [True, False])
+def test_step_through_host_equals_device_steps(gpu, fit):
+    """The end-to-end form (f copied in from and out to pinned host buffers
+    every step, the copies on their own streams overlapping the other
+    species' kernels) gives bit for bit the f of the same steps run on the
+    device."""
+    from paper_2109_06743_gb300.driver import Simulation
+    torch = gpu
+    cfg = W.harris(nx=32, ny=16, nv=8, lx=6.4, ly=3.2)
+    f0 = W.harris_state(cfg, dtype=np.float32)
+    a = Simulation(cfg, f0, None, W.harris_yee(cfg), fit=fit)
+    b = Simulation(cfg, f0, None, W.harris_yee(cfg), fit=fit)
+    host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in b.f]
+    for h, f in zip(host, b.f):
+        h.copy_(f)
+    for _ in range(4):
+        a.step()
+        b.step_through_host(host)
+    b.wait_host()
+    torch.cuda.synchronize()
+    for k in range(2):
+        assert torch.equal(host[k], a.f[k].cpu())
+    a.close()
+    b.close()
