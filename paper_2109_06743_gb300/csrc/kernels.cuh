@@ -87,6 +87,7 @@ struct VelocityArgs {
     int nv;                 // cubic block edge (2D3V); 1D1V: line length
     int nshear;
     int nbuf;               // block buffers in shared memory (set by the launcher)
+    int vec;                // f is 16-byte aligned: write blocks back with 16-byte stores (set by the launcher)
     double qm, dt;
     double vmin[3], dv[3];
     MomConv conv;

@@ -293,10 +293,15 @@ void make_mom_conv(const double* vmin, const double* dv, int n, MomConv* out) {
 
 // ---------------------------------------------------------------- kernels
 
+constexpr int vel_threads(int n) { return ((n * n + 31) / 32) * 32; }
+
+// Block copies with the CTA's compile-time thread count, so the loops unroll
+// and (for N^2 a multiple of 32) every index step is a constant.
 template <typename T, int N>
 __device__ __forceinline__ void load_block(T* blk, const T* src) {
-    constexpr int V = N * N * N;
-    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+    constexpr int V = N * N * N, NTH = vel_threads(N);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < V; e += NTH) {
         int i = e % N, jk = e / N;
         blk[jk * (N + 1) + i] = src[e];
     }
@@ -306,8 +311,9 @@ __device__ __forceinline__ void load_block(T* blk, const T* src) {
 // padding breaks 16-byte alignment of the rows, so element-sized copies)
 template <typename T, int N>
 __device__ __forceinline__ void prefetch_block(T* blk, const T* src) {
-    constexpr int V = N * N * N;
-    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+    constexpr int V = N * N * N, NTH = vel_threads(N);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < V; e += NTH) {
         const int i = e % N, jk = e / N;
         const unsigned d = (unsigned)__cvta_generic_to_shared(blk + jk * (N + 1) + i);
         if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + e) : "memory");
@@ -315,12 +321,34 @@ __device__ __forceinline__ void prefetch_block(T* blk, const T* src) {
     }
 }
 
+// write the block back; with vec (16-byte aligned f) in 16-byte stores: a
+// row holds N values (N a multiple of 4), so each group of 16 bytes comes
+// from one padded row
 template <typename T, int N>
-__device__ __forceinline__ void store_block(T* dst, const T* blk) {
-    constexpr int V = N * N * N;
-    for (int e = threadIdx.x; e < V; e += blockDim.x) {
-        int i = e % N, jk = e / N;
-        dst[e] = blk[jk * (N + 1) + i];
+__device__ __forceinline__ void store_block(T* dst, const T* blk, bool vec) {
+    constexpr int V = N * N * N, NTH = vel_threads(N);
+    constexpr int per = 16 / (int)sizeof(T);
+    static_assert(N % 4 == 0, "rows of whole 16-byte groups");
+    if (!vec) {
+#pragma unroll 4
+        for (int e = threadIdx.x; e < V; e += NTH) {
+            const int i = e % N, jk = e / N;
+            dst[e] = blk[jk * (N + 1) + i];
+        }
+        return;
+    }
+#pragma unroll 4
+    for (int g = threadIdx.x; g < V / per; g += NTH) {
+        const int e = g * per;
+        const int i = e % N, jk = e / N;
+        const T* row = blk + jk * (N + 1) + i;
+        if (sizeof(T) == 4) {
+            const float4 v = make_float4((float)row[0], (float)row[1], (float)row[2], (float)row[3]);
+            *reinterpret_cast<float4*>(dst + e) = v;
+        } else {
+            const double2 v = make_double2((double)row[0], (double)row[1]);
+            *reinterpret_cast<double2*>(dst + e) = v;
+        }
     }
 }
 
@@ -328,7 +356,6 @@ __device__ __forceinline__ void store_block(T* dst, const T* blk) {
 // a.nbuf == 2 the next cell's block is copied in while the current one is
 // advected. Registers are capped at 64 per thread (FP32) or 128 (FP64)
 // where the block size allows, so that several CTAs share an SM.
-constexpr int vel_threads(int n) { return ((n * n + 31) / 32) * 32; }
 constexpr int vel_min_blocks(int n, int es) {
     return 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) > 0 ? 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) : 1;
 }
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) 
             __syncthreads();
         }
         if (a.mom_out) block_moments<T, N>(blk, red, a.mom_out + cell * 20, a.conv);
-        store_block<T, N>(f + cell * V, blk);
+        store_block<T, N>(f + cell * V, blk, a.vec != 0);
         __syncthreads();
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -470,6 +497,7 @@ static cudaError_t launch_velocity_n(const VelocityArgs& a, cudaStream_t st) {
     VelocityArgs b = a;
     // double buffering while two buffers leave room for two CTAs per SM
     b.nbuf = 2 * blk <= 100 * 1024 ? 2 : 1;
+    b.vec = reinterpret_cast<uintptr_t>(a.f) % 16 == 0;
     size_t smem = blk * b.nbuf + sizeof(double) * (20 * 32 + 20) + sizeof(T) * (20 + 3 * N + 3);
     cudaFuncSetAttribute(velocity_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
