@@ -45,21 +45,39 @@ __device__ __forceinline__ void line_products_z(T (&m)[20], T S0, T S1, T S2, T 
 // final binomial expansion runs in FP64 (on GB300 an FP64 warp instruction
 // occupies the pipe for many cycles however few lanes are active, so FP64
 // work stays on one warp).
+//
+// The warp stage is a reduce-scatter: at each of the five butterfly steps a
+// lane keeps one half of its values (the lower or upper one, by the bit of
+// its lane index) and adds the other half of its partner's, so 20 values
+// take 10 + 5 + 3 + 2 + 1 shuffles instead of 5 each, and at the end lane
+// L holds the warp sum of one moment (20 of the 32 lanes; the rest hold
+// padding).
+template <typename T>
+__device__ __forceinline__ T rs_step(T keep_lo, T keep_hi, bool hi, int o) {
+    const T send = hi ? keep_lo : keep_hi;
+    return (hi ? keep_hi : keep_lo) + __shfl_xor_sync(0xffffffffu, send, o);
+}
+
 template <typename T>
 __device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* out, const MomConv& conv) {
     const int t = threadIdx.x;
-#pragma unroll
-    for (int a = 0; a < 20; ++a) {
-        T v = m[a];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        m[a] = v;
-    }
     const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
-    T* part = reinterpret_cast<T*>(red);
-    if (lane == 0)
+    T a[10], b[5], c[3], d[2];
 #pragma unroll
-        for (int a = 0; a < 20; ++a) part[warp * 20 + a] = m[a];
+    for (int q = 0; q < 10; ++q) a[q] = rs_step<T>(m[q], m[10 + q], lane & 16, 16);  // moments hi*10 + q
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = rs_step<T>(a[q], a[5 + q], lane & 8, 8);      // + (lane & 8 ? 5 : 0)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = rs_step<T>(b[q], q + 3 < 5 ? b[q + 3] : T(0), lane & 4, 4);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) d[q] = rs_step<T>(c[q], q + 2 < 3 ? c[q + 2] : T(0), lane & 2, 2);
+    const T e = rs_step<T>(d[0], d[1], lane & 1, 1);
+    // the moment this lane now holds: groups of 10, 5, then 3 + 2 slots
+    const int o = ((lane & 4) ? 3 : 0) + ((lane & 2) ? 2 : 0) + ((lane & 1) ? 1 : 0);
+    const bool valid = o < ((lane & 4) ? 5 : 3);
+    const int idx = ((lane & 16) ? 10 : 0) + ((lane & 8) ? 5 : 0) + o;
+    T* part = reinterpret_cast<T*>(red);
+    if (valid) part[warp * 20 + idx] = e;
     __syncthreads();
     double* im = red + 20 * 32;
     if (t < 20) {
