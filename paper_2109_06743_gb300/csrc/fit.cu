@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
     __shared__ double red[20 * 32 + 20];
     __shared__ T ssum[32];
     __shared__ T sscale;
-    __shared__ int sneg[32];
     __shared__ T spar[2 * kPar];
     __shared__ double gtab[2][sizeof(T) == 8 ? 2 * N - 1 : 1];
     T* f = reinterpret_cast<T*>(a.f);
@@ -263,33 +262,31 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
             gtab[w][sizeof(T) == 8 ? t % (2 * N - 1) : 0] = exp(-hz * (double)(m * m));
         }
         __syncthreads();
-        T lsum = T(0);
         int neg = 0;
         if (active && !skip) {
             add_maxwellian<N>(r, spar, i, j, T(-1), gtab[0]);
             add_maxwellian<N>(r, spar + kPar, i, j, T(1), gtab[1]);
+            T mn = r[0];
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-                neg |= r[k] < T(0);
-                lsum += fmax(r[k], T(0));
-            }
+            for (int k = 1; k < N; ++k) mn = fmin(mn, r[k]);
+            neg = mn < T(0);
         }
-        // block reduction: any negative; per-warp sums of the clipped values
-        // (partial sums in T, then FP64 across warps in the rare clipped case)
-        T ls = lsum;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-        const int nn = __any_sync(0xffffffffu, neg);
-        if (lane == 0) {
-            ssum[warp] = ls;
-            sneg[warp] = nn;
-        }
-        __syncthreads();
-        int anyneg = 0;
-        for (int w = 0; w < nwarp; ++w) anyneg |= sneg[w];
+        // any negative value in the block? (the clipped sums are only formed
+        // in that rare case)
+        const int anyneg = __syncthreads_or(neg);
         T scale = T(1);
         if (anyneg && !skip) {
-            // one thread forms the rescale factor in FP64
+            // per-warp sums of the clipped values in T, then FP64 across warps
+            // on one thread for the rescale factor
+            T ls = T(0);
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) ls += fmax(r[k], T(0));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+            if (lane == 0) ssum[warp] = ls;
+            __syncthreads();
             if (t == 0) {
                 double tot = 0.0;
                 for (int w = 0; w < nwarp; ++w) tot += (double)ssum[w];
