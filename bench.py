@@ -246,6 +246,7 @@ def subdomain_accuracy(mlp_w, device, steps=2, sample=(64, 32)):
         abi.mlp_set_weights(sim.ctx, mlp_w)
     ost = OracleState(cfg, [x.astype(np.float64) for x in f32], None, yee)
     e0_gpu, e0_or = sim.total_energy(), ost.total_energy()
+    psi0 = ost.reconnected_flux()
     t0 = time.perf_counter()
     for _ in range(steps):
         ost.step(cfg.dt)
@@ -270,12 +271,16 @@ def subdomain_accuracy(mlp_w, device, steps=2, sample=(64, 32)):
                           for a, b, c_ in powers], axis=1) + 1e-300
         mom.append(float((np.abs(mg - mo) / scale).max()))
     e1_gpu, e1_or = sim.total_energy(), ost.total_energy()
+    psi_gpu, psi_or = sim.reconnected_flux(), ost.reconnected_flux()
     sim.close()
     cells = cfg.phase_cells() * steps
     return {"subdomain": "%dx%d x 16^3 per species, 2 species, %d steps, dx, dv, dt of the workload" % (nx, ny, steps),
             "f_l1_rel_error": max(l1), "moment_max_rel_error": max(mom),
             "energy_drift_gpu": (e1_gpu - e0_gpu) / e0_gpu, "energy_drift_oracle": (e1_or - e0_or) / e0_or,
-            "energy_gpu_vs_oracle": (e1_gpu - e1_or) / e1_or}, {
+            "energy_gpu_vs_oracle": (e1_gpu - e1_or) / e1_or,
+            "reconnected_flux_rel_error": abs(psi_gpu - psi_or) / psi_or,
+            "reconnection_rate_gpu": (psi_gpu - psi0) / (steps * cfg.dt),
+            "reconnection_rate_oracle": (psi_or - psi0) / (steps * cfg.dt)}, {
         "value": cells / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
         "sample": "%d oracle steps of the Harris sheet on a %dx%d x 16^3 subdomain (2 species, %d cells, same dx, "
                   "dv, dt as the workload), FP64, one host core, %.1f s" % (steps, nx, ny, cfg.phase_cells(), t_or)}

@@ -253,6 +253,17 @@ class Simulation:
         kin, ee, eb = self.energies()
         return sum(kin) + ee + eb
 
+    def reconnected_flux(self):
+        """Reconnected flux of the GEM set-up (Sec. 3.3): with B_y = -dA_z/dx
+        on the sheet's midline (the integer Yee row at y = 0), half the
+        integral of |B_y| over x, i.e. max A_z - min A_z along the midline for
+        one X and one O point (diagnostic only)."""
+        cfg = self.cfg
+        self.stream.synchronize()
+        y = self.yee.cpu().numpy().reshape(6, cfg.ny + 1, cfg.nx)
+        jm = int(round(-cfg.y0 / cfg.dy))
+        return 0.5 * np.abs(y[4, jm]).sum() * cfg.dx
+
 
 class ClosureFluid:
     """The stand-alone ten-moment fluid model with the gradient heat-flux

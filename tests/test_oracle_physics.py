@@ -147,3 +147,15 @@ def test_two_stream_root_against_direct_quadrature():
     assert abs(eps_quad(wr + 1j * wi)) < 1e-7
     for w in (0.3 + 0.4j, -0.7 + 0.9j):
         assert abs(eps_quad(w) - eps(w)) < 1e-7
+
+
+def test_reconnected_flux_of_the_initial_harris_fields(orc):
+    """The GEM diagnostic (Sec. 3.3): on the sheet's midline A_z =
+    psi0 cos(2 pi x / L), whose variation over one period is 4 psi0, so the
+    reconnected flux (half the integral of |B_y|) of the initial fields is
+    2 psi0 exactly; doubling the perturbation doubles it."""
+    from oracle.step import OracleState
+    for psi0 in (0.1, 0.2):
+        cfg = W.harris(nx=32, ny=16, nv=8, lx=6.4, ly=3.2, psi0=psi0)
+        st = OracleState(cfg, W.harris_state(cfg), None, W.harris_yee(cfg))
+        assert abs(st.reconnected_flux() - 2 * psi0) < 1e-12
