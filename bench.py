@@ -45,23 +45,50 @@ METRIC = "phase-space cell updates/s per step (FP32+MLP vs FP64 GPU) and % HBM r
 UNIT = "cell-updates/s"
 
 WORKLOADS = {
-    # name: (nx, ny, nv, lx, ly)  -- Harris sheet, both species
-    "harris_512x256_v16": (512, 256, 16, 25.6, 12.8),
-    "harris_256x128_v16": (256, 128, 16, 25.6, 12.8),
-    "harris_128x64_v20": (128, 64, 20, 25.6, 12.8),
-    "harris_128x64_v16": (128, 64, 16, 25.6, 12.8),
+    # name: (sheet, nx, ny, nv, lx, ly), both species
+    "harris_512x256_v16": ("harris", 512, 256, 16, 25.6, 12.8),
+    "harris_256x128_v16": ("harris", 256, 128, 16, 25.6, 12.8),
+    "harris_128x64_v20": ("harris", 128, 64, 20, 25.6, 12.8),
+    "harris_128x64_v16": ("harris", 128, 64, 16, 25.6, 12.8),
+    # asymmetric (magnetopause-like) sheet: density ratio 10, temperature
+    # ratio 3, guide field 0.1, m_i/m_e = 100
+    "asym_1024x512_v12": ("asym", 1024, 512, 12, 51.2, 25.6),
+    "asym_256x128_v12": ("asym", 256, 128, 12, 12.8, 6.4),
 }
 # warm-start network: trained on the fits of a smaller run with the same
 # velocity grid (the network's inputs are in units of the velocity cells)
 TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "harris_128x64_v16",
-              "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16"}
+              "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16",
+              "asym_1024x512_v12": "asym_256x128_v12", "asym_256x128_v12": "asym_256x128_v12"}
 
 
-def make_cfg(name, precision=32):
+def make_cfg(name, precision=32, sub=None):
+    """The named workload; with sub = (nx, ny) the central subdomain of it
+    with the same dx, dy, velocity grid and dt."""
     from paper_2109_06743_gb300 import workloads as W
-    nx, ny, nv, lx, ly = WORKLOADS[name]
-    cfg = W.harris(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
-    return cfg
+    kind, nx, ny, nv, lx, ly = WORKLOADS[name]
+    if sub is not None:
+        lx, ly = lx * sub[0] / nx, ly * sub[1] / ny
+        nx, ny = sub
+    make = W.harris if kind == "harris" else W.asym_sheet
+    return make(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
+
+
+def initial_state(cfg, dtype):
+    from paper_2109_06743_gb300 import workloads as W
+    return (W.asym_state if cfg.kind == "asym" else W.harris_state)(cfg, dtype=dtype)
+
+
+def initial_yee(cfg):
+    from paper_2109_06743_gb300 import workloads as W
+    return W.asym_yee(cfg) if cfg.kind == "asym" else W.harris_yee(cfg)
+
+
+def x_line(cfg):
+    """y of the sheet's X line: 0 for the Harris sheet, the B_x null of the
+    asymmetric one."""
+    from paper_2109_06743_gb300 import workloads as W
+    return W.asym_null_y(cfg) if cfg.kind == "asym" else 0.0
 
 
 def peaks():
@@ -193,11 +220,10 @@ def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=409
     import torch
 
     from paper_2109_06743_gb300 import abi
-    from paper_2109_06743_gb300 import workloads as W
     from paper_2109_06743_gb300.driver import Simulation
     t0 = time.perf_counter()
     cfg = make_cfg(name, precision=32)
-    sim = Simulation(cfg, W.harris_state(cfg, dtype=np.float32), None, W.harris_yee(cfg), device=device)
+    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device)
     cap = harvest_steps * 4 * cfg.ncell
     buf = torch.zeros((cap, abi.MLP_SAMPLE), dtype=torch.float32, device=device)
     abi.mlp_set_harvest(sim.ctx, buf, cap, sim.stream)
@@ -222,31 +248,47 @@ def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=409
     return w, info
 
 
-def subdomain_accuracy(mlp_w, device, steps=2, sample=(64, 32)):
+def accuracy_case(name):
+    """The FP32 run checked against the FP64 oracle: for the Harris sheet a
+    64 x 32 subdomain with the workload's dx, dv and dt (2 steps); for the
+    asymmetric sheet a downscaled run of the sheet, 64 x 32 cells over
+    6.4 x 3.2 (half the workload's resolution, five cells across the sheet
+    half-width) with the workload's velocity grid (4 steps)."""
+    from paper_2109_06743_gb300 import workloads as W
+    kind, nx, ny, nv, lx, ly = WORKLOADS[name]
+    if kind == "asym":
+        return W.asym_sheet(nx=64, ny=32, nv=nv, lx=6.4, ly=3.2, precision=32), 4
+    return make_cfg(name, precision=32, sub=(64, 32)), 2
+
+
+def subdomain_accuracy(name, mlp_w, device):
     """Accuracy of the timed form (FP32 f, warm-started fits) against the
-    FP64 oracle on a 64 x 32 x 16^3 subdomain with the workload's dx, dv and
-    dt: relative L1 error of f, the largest moment error relative to the
-    moment's absolute scale sum |v^alpha| f dv^3, and both total-energy drifts; the oracle's own time is
-    the CPU baseline (one host core)."""
+    FP64 oracle on the workload's accuracy case: relative L1 error of f, the
+    largest moment error relative to the moment's absolute scale
+    sum |v^alpha| f dv^3, both total-energy drifts, the energy partition
+    (kinetic+thermal per species, electric, magnetic) on both sides, and the
+    reconnected flux on the X line; the oracle's own time is the CPU
+    baseline (one host core)."""
     import numpy as np
 
     import oracle
     from oracle.step import OracleState
     from paper_2109_06743_gb300 import abi
-    from paper_2109_06743_gb300 import workloads as W
     from paper_2109_06743_gb300.driver import Simulation
     oracle.build()
-    nx, ny = sample
-    cfg = W.harris(nx=nx, ny=ny, nv=16, lx=25.6 * nx / 512, ly=12.8 * ny / 256, precision=32)
-    f64 = W.harris_state(cfg)
+    cfg, steps = accuracy_case(name)
+    nv = cfg.species[0].nv[0]
+    f64 = initial_state(cfg, np.float64)
     f32 = [x.astype(np.float32) for x in f64]
-    yee = W.harris_yee(cfg)
+    yee = initial_yee(cfg)
+    yl = x_line(cfg)
     sim = Simulation(cfg, f32, None, yee, device=device)
     if mlp_w is not None:
         abi.mlp_set_weights(sim.ctx, mlp_w)
     ost = OracleState(cfg, [x.astype(np.float64) for x in f32], None, yee)
     e0_gpu, e0_or = sim.total_energy(), ost.total_energy()
-    psi0 = ost.reconnected_flux()
+    part0 = ost.energies()
+    psi0 = ost.reconnected_flux(yl)
     t0 = time.perf_counter()
     for _ in range(steps):
         ost.step(cfg.dt)
@@ -271,41 +313,57 @@ def subdomain_accuracy(mlp_w, device, steps=2, sample=(64, 32)):
                           for a, b, c_ in powers], axis=1) + 1e-300
         mom.append(float((np.abs(mg - mo) / scale).max()))
     e1_gpu, e1_or = sim.total_energy(), ost.total_energy()
-    psi_gpu, psi_or = sim.reconnected_flux(), ost.reconnected_flux()
+    psi_gpu, psi_or = sim.reconnected_flux(yl), ost.reconnected_flux(yl)
+
+    def channels(e):
+        kin, ee, eb = e
+        return [float(x) for x in list(kin) + [ee, eb]]
+    p_gpu, p_or, p0 = channels(sim.energies()), channels(ost.energies()), channels(part0)
     sim.close()
     cells = cfg.phase_cells() * steps
-    return {"subdomain": "%dx%d x 16^3 per species, 2 species, %d steps, dx, dv, dt of the workload" % (nx, ny, steps),
+    what = ("%dx%d x %d^3 per species, 2 species, %d steps, " % (cfg.nx, cfg.ny, nv, steps)
+            + ("downscaled whole sheet (dx %.2f), velocity grid and dt rule of the workload" % cfg.dx
+               if cfg.kind == "asym" else "dx, dv, dt of the workload"))
+    return {"run": what,
             "f_l1_rel_error": max(l1), "moment_max_rel_error": max(mom),
             "energy_drift_gpu": (e1_gpu - e0_gpu) / e0_gpu, "energy_drift_oracle": (e1_or - e0_or) / e0_or,
             "energy_gpu_vs_oracle": (e1_gpu - e1_or) / e1_or,
+            "energy_partition": {"channels": ["kinetic+thermal e", "kinetic+thermal i", "electric", "magnetic"],
+                                 "fraction_gpu": [x / sum(p_gpu) for x in p_gpu],
+                                 "fraction_oracle": [x / sum(p_or) for x in p_or],
+                                 "change_gpu": [a - b for a, b in zip(p_gpu, p0)],
+                                 "change_oracle": [a - b for a, b in zip(p_or, p0)],
+                                 "max_channel_error_rel_total": max(abs(a - b) for a, b in zip(p_gpu, p_or))
+                                 / sum(p_or)},
+            "x_line_y": yl,
             "reconnected_flux_rel_error": abs(psi_gpu - psi_or) / psi_or,
             "reconnection_rate_gpu": (psi_gpu - psi0) / (steps * cfg.dt),
             "reconnection_rate_oracle": (psi_or - psi0) / (steps * cfg.dt)}, {
         "value": cells / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": "%d oracle steps of the Harris sheet on a %dx%d x 16^3 subdomain (2 species, %d cells, same dx, "
-                  "dv, dt as the workload), FP64, one host core, %.1f s" % (steps, nx, ny, cfg.phase_cells(), t_or)}
+        "sample": "%d oracle steps of the %s sheet, %dx%d x %d^3 (2 species, %d cells), FP64, one host core, %.1f s" % (
+            steps, cfg.kind, cfg.nx, cfg.ny, nv, cfg.phase_cells(), t_or)}
 
 
-def cpu_baseline(steps=1, sample=(32, 16)):
+def cpu_baseline(name, steps=1, sample=(32, 16)):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    a 32x16 spatial subdomain with the workload's dx, dv (both species),
-    one Algorithm 1 step per timed step, single-threaded."""
+    the central sample[0] x sample[1] spatial subdomain with the workload's
+    dx, dv and dt (both species), one Algorithm 1 step per timed step,
+    single-threaded."""
     import numpy as np
 
     from oracle.step import OracleState
-    from paper_2109_06743_gb300 import workloads as W
-    nx, ny = sample
-    cfg = W.harris(nx=nx, ny=ny, nv=16, lx=25.6 * nx / 512, ly=12.8 * ny / 256, precision=64)
-    st = OracleState(cfg, W.harris_state(cfg), None, W.harris_yee(cfg))
+    cfg = make_cfg(name, precision=64, sub=sample)
+    st = OracleState(cfg, initial_state(cfg, np.float64), None, initial_yee(cfg))
     t0 = time.perf_counter()
     for _ in range(steps):
         st.step(cfg.dt)
     el = time.perf_counter() - t0
     cells = cfg.phase_cells() * steps
+    nv = cfg.species[0].nv[0]
     return {"value": cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle step(s) of the Harris sheet on a %dx%d x 16^3 subdomain (2 species, %d cells, "
+            "sample": "%d oracle step(s) of the %s sheet on a %dx%d x %d^3 subdomain (2 species, %d cells, "
                       "same dx, dv, dt as the workload), FP64, one host core, %.1f s" % (
-                          steps, nx, ny, cfg.phase_cells(), el)}
+                          steps, cfg.kind, cfg.nx, cfg.ny, nv, cfg.phase_cells(), el)}
 
 
 def run_reference(args, rank):
@@ -316,7 +374,7 @@ def run_reference(args, rank):
     oracle.build()
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; warm-up steps are not needed
-    cb = cpu_baseline(steps=args.steps, sample=(16, 8))
+    cb = cpu_baseline(args.workload, steps=args.steps, sample=(16, 8))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -352,7 +410,6 @@ def main():
 
     from paper_2109_06743_gb300 import abi
     from paper_2109_06743_gb300 import build as B
-    from paper_2109_06743_gb300 import workloads as W
     from paper_2109_06743_gb300.driver import Simulation
 
     torch.cuda.set_device(local)
@@ -370,8 +427,8 @@ def main():
     mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(TRAIN_FROM[args.workload], device)
     use_mlp = mlp_w is not None
     cfg = make_cfg(args.workload, precision=32)
-    f0 = W.harris_state(cfg, dtype=np.float32)
-    sim = Simulation(cfg, f0, None, W.harris_yee(cfg), device=device)
+    f0 = initial_state(cfg, np.float32)
+    sim = Simulation(cfg, f0, None, initial_yee(cfg), device=device)
     if use_mlp:
         abi.mlp_set_weights(sim.ctx, mlp_w)
     stream = sim.stream
@@ -489,7 +546,7 @@ def main():
     if use_mlp:
         mlp_info.update({"newton_iterations_per_fit": fit_iters, "newton_fallbacks_per_fit": stats[1] / nfits,
                          "cold_start": cold,
-                         "applied_to": args.workload + " (same 16^3-per-species velocity grid)"
+                         "applied_to": args.workload + " (same %d^3-per-species velocity grid)" % cfg.species[0].nv[0]
                          if TRAIN_FROM[args.workload] != args.workload else args.workload})
     sim.close()
     del sim
@@ -499,7 +556,7 @@ def main():
     fp64 = None
     if args.fp64_steps > 0:
         cfg64 = make_cfg(args.workload, precision=64)
-        s64 = Simulation(cfg64, W.harris_state(cfg64, dtype=np.float64), None, W.harris_yee(cfg64),
+        s64 = Simulation(cfg64, initial_state(cfg64, np.float64), None, initial_yee(cfg64),
                          device="cuda:%d" % local)
         for _ in range(3):
             s64.step()
@@ -518,7 +575,7 @@ def main():
 
     if rank != 0:
         return 0
-    acc, cb = (None, None) if args.no_cpu else subdomain_accuracy(mlp_w, device)
+    acc, cb = (None, None) if args.no_cpu else subdomain_accuracy(args.workload, mlp_w, device)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,

@@ -142,12 +142,12 @@ class OracleState:
         kin, ee, eb = self.energies()
         return sum(kin) + ee + eb
 
-    def reconnected_flux(self):
-        """psi = (1/2) sum_x |B_y(x, y = 0)| dx on the integer Yee row of the
-        midline (GEM diagnostic, Sec. 3.3)."""
+    def reconnected_flux(self, y_line=0.0):
+        """psi = (1/2) sum_x |B_y(x, y_line)| dx on the integer Yee row nearest
+        the midline y_line (GEM diagnostic, Sec. 3.3)."""
         cfg = self.cfg
         By = self.yee.reshape(6, cfg.ny + 1, cfg.nx)[4]
-        row = int(round((0.0 - cfg.y0) / cfg.dy))
+        row = int(round((y_line - cfg.y0) / cfg.dy))
         return 0.5 * float(np.sum(np.abs(By[row]))) * cfg.dx
 
     def mass(self):

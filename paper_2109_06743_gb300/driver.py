@@ -253,15 +253,16 @@ class Simulation:
         kin, ee, eb = self.energies()
         return sum(kin) + ee + eb
 
-    def reconnected_flux(self):
+    def reconnected_flux(self, y_line=0.0):
         """Reconnected flux of the GEM set-up (Sec. 3.3): with B_y = -dA_z/dx
-        on the sheet's midline (the integer Yee row at y = 0), half the
+        on the sheet's midline (the integer Yee row nearest y_line: y = 0 for
+        a symmetric sheet, the B_x null of an asymmetric one), half the
         integral of |B_y| over x, i.e. max A_z - min A_z along the midline for
         one X and one O point (diagnostic only)."""
         cfg = self.cfg
         self.stream.synchronize()
         y = self.yee.cpu().numpy().reshape(6, cfg.ny + 1, cfg.nx)
-        jm = int(round(-cfg.y0 / cfg.dy))
+        jm = int(round((y_line - cfg.y0) / cfg.dy))
         return 0.5 * np.abs(y[4, jm]).sum() * cfg.dx
 
 

@@ -313,6 +313,13 @@ def asym_profiles(cfg, y):
     return (p0 - 0.5 * bx * bx) / tt, tt, bx
 
 
+def asym_null_y(cfg):
+    """y of the B_x null of the unperturbed asymmetric sheet, where
+    tanh(y/lam) = (B2 - B1)/(B1 + B2): the midline of its X line."""
+    n1, t1, b1, n2, t2, b2, p0 = _asym_fields(cfg)
+    return cfg.lam * math.atanh((b2 - b1) / (b1 + b2))
+
+
 def asym_state(cfg: Config, dtype=np.float64):
     """Initial f per species of the asymmetric sheet: Maxwellians with the
     local density and temperature (T_i / T_e = 5 everywhere), drifting in z

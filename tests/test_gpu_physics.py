@@ -133,3 +133,42 @@ def test_harris_ablation_energy_error_grows_on_coarser_velocity_grids(gpu):
     assert abs(drift[20, True]) < 1e-4 and abs(drift[12, True]) < 1e-4, drift
     assert abs(drift[20, False]) > 10 * abs(drift[20, True]), drift
     assert abs(drift[12, False]) > abs(drift[20, False]), drift
+
+
+def test_asymmetric_sheet_downscaled_reconnection_and_energy_partition(gpu, orc):
+    """The asymmetric (magnetopause-like) sheet downscaled to 32 x 16 cells
+    over 3.2 x 1.6 (dx = 0.1, five cells across the sheet half-width) with
+    its 12^3 velocity grids: the FP32 form (FP32 f and sweeps, FP64 moment
+    sums and fields, fitted) against the FP64 oracle over 12 steps. Each
+    energy channel (kinetic+thermal of either species, electric, magnetic)
+    agrees to 1e-5 of the total (the FP32 moment tolerance), and the total
+    drifts by less than 1e-4 on both sides; the reconnected flux on the X
+    line (the B_x null) agrees to 1e-6 and its change, the reconnection
+    rate, to 1% of the oracle's."""
+    from oracle.step import OracleState
+    from paper_2109_06743_gb300.driver import Simulation
+    cfg = W.asym_sheet(nx=32, ny=16, nv=12, lx=3.2, ly=1.6, precision=32)
+    f = [x.astype(np.float32) for x in W.asym_state(cfg)]
+    yee = W.asym_yee(cfg)
+    yl = W.asym_null_y(cfg)
+    sim = Simulation(cfg, f, None, yee)
+    ost = OracleState(cfg, [x.astype(np.float64) for x in f], None, yee)
+    psi0 = ost.reconnected_flux(yl)
+    assert abs(sim.reconnected_flux(yl) - psi0) < 1e-15 * psi0 + 1e-300
+    E0g, E0o = sim.total_energy(), ost.total_energy()
+    steps = 12
+    for _ in range(steps):
+        sim.step()
+        ost.step(cfg.dt)
+    kg, eeg, ebg = sim.energies()
+    ko, eeo, ebo = ost.energies()
+    total = sum(ko) + eeo + ebo
+    for a, b in zip(list(kg) + [eeg, ebg], list(ko) + [eeo, ebo]):
+        assert abs(a - b) <= 1e-5 * total, (a, b, total)
+    assert abs(total / E0o - 1) < 1e-4 and abs(sim.total_energy() / E0g - 1) < 1e-4
+    pg, po = sim.reconnected_flux(yl), ost.reconnected_flux(yl)
+    assert abs(pg - po) <= 1e-6 * po, (pg, po)
+    rg, ro = (pg - psi0) / (steps * cfg.dt), (po - psi0) / (steps * cfg.dt)
+    assert ro != 0.0 and abs(rg - ro) <= 1e-2 * abs(ro), (rg, ro)
+    assert sim.stats()[3] == 0
+    sim.close()

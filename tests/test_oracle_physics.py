@@ -159,3 +159,28 @@ def test_reconnected_flux_of_the_initial_harris_fields(orc):
         cfg = W.harris(nx=32, ny=16, nv=8, lx=6.4, ly=3.2, psi0=psi0)
         st = OracleState(cfg, W.harris_state(cfg), None, W.harris_yee(cfg))
         assert abs(st.reconnected_flux() - 2 * psi0) < 1e-12
+
+
+def test_reconnected_flux_of_the_initial_asymmetric_fields(orc):
+    """On the asymmetric sheet the X line lies on the B_x null,
+    y_n = lam artanh((B2 - B1)/(B1 + B2)) (below y = 0: B2 < B1), and the
+    initial A_z on that row is the Gaussian X-line bump xi exp(-(x^2 + y^2) /
+    (4 lam^2)) over a flat profile, plus corner noise of at most 1e-6 dy:
+    its variation over a period is twice the bump's height above its edge
+    value, so psi = xi exp(-y^2 / (4 lam^2)) (1 - exp(-(L/2)^2 / (4 lam^2)))
+    up to the noise's total variation (2 n_x 1e-6 dy)."""
+    from oracle.step import OracleState
+    cfg = W.asym_sheet(nx=32, ny=32, nv=8, lx=6.4, ly=6.4)
+    yn = W.asym_null_y(cfg)
+    b2 = math.sqrt(1.0 + 2.0 * (0.1 * 1.5 - 0.5))
+    assert abs(yn - 0.5 * math.atanh((b2 - 1.0) / (1.0 + b2))) < 1e-15 and -0.2 < yn < -0.1
+    st = OracleState(cfg, W.asym_state(cfg), None, W.asym_yee(cfg))
+    row = round((yn - cfg.y0) / cfg.dy)
+    y = cfg.y0 + row * cfg.dy
+    lam2 = 4 * cfg.lam ** 2
+    want = cfg.xi * math.exp(-y * y / lam2) * (1 - math.exp(-(cfg.nx * cfg.dx / 2) ** 2 / lam2))
+    got = st.reconnected_flux(yn)
+    assert abs(got - want) <= 2 * cfg.nx * 1e-6 * cfg.dy, (got, want)
+    # on the row of y = 0 (one row up) the bump is at its full height xi
+    want0 = cfg.xi * (1 - math.exp(-(cfg.nx * cfg.dx / 2) ** 2 / lam2))
+    assert abs(st.reconnected_flux(0.0) - want0) <= 2 * cfg.nx * 1e-6 * cfg.dy
