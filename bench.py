@@ -29,7 +29,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -44,51 +43,9 @@ if ROOT not in sys.path:
 METRIC = "phase-space cell updates/s per step (FP32+MLP vs FP64 GPU) and % HBM roofline"
 UNIT = "cell-updates/s"
 
-WORKLOADS = {
-    # name: (sheet, nx, ny, nv, lx, ly), both species
-    "harris_512x256_v16": ("harris", 512, 256, 16, 25.6, 12.8),
-    "harris_256x128_v16": ("harris", 256, 128, 16, 25.6, 12.8),
-    "harris_128x64_v20": ("harris", 128, 64, 20, 25.6, 12.8),
-    "harris_128x64_v16": ("harris", 128, 64, 16, 25.6, 12.8),
-    # asymmetric (magnetopause-like) sheet: density ratio 10, temperature
-    # ratio 3, guide field 0.1, m_i/m_e = 100
-    "asym_1024x512_v12": ("asym", 1024, 512, 12, 51.2, 25.6),
-    "asym_256x128_v12": ("asym", 256, 128, 12, 12.8, 6.4),
-}
-# warm-start network: trained on the fits of a smaller run with the same
-# velocity grid (the network's inputs are in units of the velocity cells)
-TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "harris_128x64_v16",
-              "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16",
-              "asym_1024x512_v12": "asym_256x128_v12", "asym_256x128_v12": "asym_256x128_v12"}
-
-
-def make_cfg(name, precision=32, sub=None):
-    """The named workload; with sub = (nx, ny) the central subdomain of it
-    with the same dx, dy, velocity grid and dt."""
-    from paper_2109_06743_gb300 import workloads as W
-    kind, nx, ny, nv, lx, ly = WORKLOADS[name]
-    if sub is not None:
-        lx, ly = lx * sub[0] / nx, ly * sub[1] / ny
-        nx, ny = sub
-    make = W.harris if kind == "harris" else W.asym_sheet
-    return make(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
-
-
-def initial_state(cfg, dtype):
-    from paper_2109_06743_gb300 import workloads as W
-    return (W.asym_state if cfg.kind == "asym" else W.harris_state)(cfg, dtype=dtype)
-
-
-def initial_yee(cfg):
-    from paper_2109_06743_gb300 import workloads as W
-    return W.asym_yee(cfg) if cfg.kind == "asym" else W.harris_yee(cfg)
-
-
-def x_line(cfg):
-    """y of the sheet's X line: 0 for the Harris sheet, the B_x null of the
-    asymmetric one."""
-    from paper_2109_06743_gb300 import workloads as W
-    return W.asym_null_y(cfg) if cfg.kind == "asym" else 0.0
+from paper_2109_06743_gb300.workloads import NAMED as WORKLOADS  # noqa: E402
+from paper_2109_06743_gb300.workloads import TRAIN_FROM, initial_state, initial_yee, x_line  # noqa: E402
+from paper_2109_06743_gb300.workloads import named as make_cfg  # noqa: E402
 
 
 def peaks():
@@ -211,41 +168,6 @@ def job_rate(units_per_rank, steps, world, seconds):
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time (replicas: every rank processes the same workload)."""
     return units_per_rank * steps * world / seconds
-
-
-def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=4096, lr=2e-3):
-    """Harvest (inputs, eta* - eta_0) samples from the converged fits of a
-    cold-started run, train the network on the GPU, return its weights."""
-    import numpy as np
-    import torch
-
-    from paper_2109_06743_gb300 import abi
-    from paper_2109_06743_gb300.driver import Simulation
-    t0 = time.perf_counter()
-    cfg = make_cfg(name, precision=32)
-    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device)
-    cap = harvest_steps * 4 * cfg.ncell
-    buf = torch.zeros((cap, abi.MLP_SAMPLE), dtype=torch.float32, device=device)
-    abi.mlp_set_harvest(sim.ctx, buf, cap, sim.stream)
-    for _ in range(harvest_steps):
-        sim.step()
-    n = abi.mlp_harvest_count(sim.ctx, sim.stream)
-    abi.mlp_set_harvest(sim.ctx, None, 0, sim.stream)
-    abi.mlp_init(sim.ctx, 2109)
-    abi.mlp_normalize(sim.ctx, buf, n, sim.stream)
-    t1 = time.perf_counter()
-    losses = abi.mlp_train(sim.ctx, buf, n, train_steps, batch=batch, lr=lr, seed=6743, record_loss=True,
-                           stream=sim.stream)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    w = abi.mlp_get_weights(sim.ctx)
-    sim.close()
-    del buf
-    info = {"trained_on": "%s, %d cold-started steps" % (name, harvest_steps), "samples": int(n),
-            "train_steps": train_steps, "batch": batch, "lr": lr,
-            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
-            "harvest_seconds": t1 - t0, "train_seconds": t2 - t1}
-    return w, info
 
 
 def accuracy_case(name):
@@ -411,6 +333,7 @@ def main():
     from paper_2109_06743_gb300 import abi
     from paper_2109_06743_gb300 import build as B
     from paper_2109_06743_gb300.driver import Simulation
+    from paper_2109_06743_gb300.warmstart import train_warm_start
 
     torch.cuda.set_device(local)
     dist = None

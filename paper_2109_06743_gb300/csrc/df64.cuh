@@ -59,6 +59,12 @@ __device__ __forceinline__ df2 df2_mulf(df2 a, float b) {
     e = fmaf(a.lo, b, e);
     return df2_qtwo_sum(p, e);
 }
+// a / b: FP32 quotient, then one correction from the double-float remainder
+__device__ __forceinline__ df2 df2_div(df2 a, df2 b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df2 r = df2_sub(a, df2_mulf(b, q1));
+    return df2_qtwo_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
 // a * b + c
 __device__ __forceinline__ df2 df2_fma(df2 a, df2 b, df2 c) { return df2_add(df2_mul(a, b), c); }
 

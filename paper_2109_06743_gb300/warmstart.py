@@ -1,0 +1,47 @@
+"""Training of the moment-fit warm-start network on the fits of a
+cold-started run (the learned part of the moment fit: the network maps a
+cell's target moments to a warm start of its Newton fit, Sec. 2.2 with
+Algorithm 1's fit). The samples are harvested by the Newton kernel from its
+converged fits; normalisation, training (BF16 tensor-core GEMMs, FP32
+accumulation, Adam) and inference run in the library's kernels."""
+import time
+
+import numpy as np
+import torch
+
+from . import abi
+from . import workloads as W
+from .driver import Simulation
+
+
+def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=4096, lr=2e-3):
+    """Harvest (inputs, eta* - eta_0) samples from the converged fits of
+    harvest_steps cold-started steps of the named workload, train the
+    warm-start network on the GPU with the project's own kernels, and return
+    its weights and a summary (sample count, first and last losses,
+    seconds)."""
+    t0 = time.perf_counter()
+    cfg = W.named(name, precision=32)
+    sim = Simulation(cfg, W.initial_state(cfg, np.float32), None, W.initial_yee(cfg), device=device)
+    cap = harvest_steps * 4 * cfg.ncell
+    buf = torch.zeros((cap, abi.MLP_SAMPLE), dtype=torch.float32, device=device)
+    abi.mlp_set_harvest(sim.ctx, buf, cap, sim.stream)
+    for _ in range(harvest_steps):
+        sim.step()
+    n = abi.mlp_harvest_count(sim.ctx, sim.stream)
+    abi.mlp_set_harvest(sim.ctx, None, 0, sim.stream)
+    abi.mlp_init(sim.ctx, 2109)
+    abi.mlp_normalize(sim.ctx, buf, n, sim.stream)
+    t1 = time.perf_counter()
+    losses = abi.mlp_train(sim.ctx, buf, n, train_steps, batch=batch, lr=lr, seed=6743, record_loss=True,
+                           stream=sim.stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    w = abi.mlp_get_weights(sim.ctx)
+    sim.close()
+    del buf
+    info = {"trained_on": "%s, %d cold-started steps" % (name, harvest_steps), "samples": int(n),
+            "train_steps": train_steps, "batch": batch, "lr": lr,
+            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+            "harvest_seconds": t1 - t0, "train_seconds": t2 - t1}
+    return w, info

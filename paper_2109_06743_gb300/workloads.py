@@ -485,3 +485,50 @@ def orszag_tang_fluid(cfg: Config):
         U[..., 9] = n * (th + uz * uz)
         out.append(U.reshape(cfg.ncell, 10))
     return out
+
+
+# ------------------------------------------------------- named workloads ---
+
+NAMED = {
+    # name: (sheet, nx, ny, nv, lx, ly), both species
+    "harris_512x256_v16": ("harris", 512, 256, 16, 25.6, 12.8),
+    "harris_256x128_v16": ("harris", 256, 128, 16, 25.6, 12.8),
+    "harris_128x64_v20": ("harris", 128, 64, 20, 25.6, 12.8),
+    "harris_128x64_v16": ("harris", 128, 64, 16, 25.6, 12.8),
+    # asymmetric (magnetopause-like) sheet: density ratio 10, temperature
+    # ratio 3, guide field 0.1, m_i/m_e = 100
+    "asym_1024x512_v12": ("asym", 1024, 512, 12, 51.2, 25.6),
+    "asym_256x128_v12": ("asym", 256, 128, 12, 12.8, 6.4),
+}
+# warm-start network: trained on the fits of a smaller run with the same
+# velocity grid (the network's inputs are in units of the velocity cells)
+TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "harris_128x64_v16",
+              "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16",
+              "asym_1024x512_v12": "asym_256x128_v12", "asym_256x128_v12": "asym_256x128_v12"}
+
+
+def named(name, precision=32, sub=None) -> Config:
+    """The named workload; with sub = (nx, ny) the central subdomain of it
+    with the same dx, dy, velocity grid and dt."""
+    kind, nx, ny, nv, lx, ly = NAMED[name]
+    if sub is not None:
+        lx, ly = lx * sub[0] / nx, ly * sub[1] / ny
+        nx, ny = sub
+    make = harris if kind == "harris" else asym_sheet
+    return make(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
+
+
+def initial_state(cfg: Config, dtype=np.float64):
+    """Initial f of a Harris or asymmetric sheet configuration."""
+    return (asym_state if cfg.kind == "asym" else harris_state)(cfg, dtype=dtype)
+
+
+def initial_yee(cfg: Config):
+    """Initial Yee fields of a Harris or asymmetric sheet configuration."""
+    return asym_yee(cfg) if cfg.kind == "asym" else harris_yee(cfg)
+
+
+def x_line(cfg: Config):
+    """y of the sheet's X line: 0 for the Harris sheet, the B_x null of the
+    asymmetric one."""
+    return asym_null_y(cfg) if cfg.kind == "asym" else 0.0

@@ -283,6 +283,57 @@ def test_moment_fit_matches_oracle(gpu, orc, precision, nv):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nv", [12, 16])
+def test_moment_fit_of_narrow_maxwellians_stays_on_the_fast_path(gpu, orc, precision, nv):
+    """Cells of the asymmetric sheet: the velocity boxes are sized for the
+    hot side, so on the dense cold side a Maxwellian falls by e^-37 per axis
+    towards the box faces and by more than e^-100 into the corners, beyond
+    the float range. The centre-out recurrences of the fit still evaluate
+    every block on the fast path (the counter of FP64-exponential
+    evaluations stays 0), and the fit equals the oracle's as in the test
+    above."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = W.asym_sheet(nx=3, ny=16, nv=nv, lx=0.6, ly=6.4, precision=precision)
+    cfg.fit_tol = 1e-12
+    # the spread of the exponent over the box (centre to corner), per cell
+    _, yc = np.meshgrid(cfg.x0 + (np.arange(cfg.nx) + 0.5) * cfg.dx, cfg.y0 + (np.arange(cfg.ny) + 0.5) * cfg.dy)
+    _, tt, _ = W.asym_profiles(cfg, yc.reshape(-1))
+    spread = [3 * sp.vmax[0] ** 2 / (2 * (1 / 6 if sp.name == "e" else 5 / 6) * tt / sp.m) for sp in cfg.species]
+    assert min(s.max() for s in spread) > 100
+    rng = np.random.default_rng(410)
+    f0 = [cast(np.ascontiguousarray(f.reshape(cfg.ncell, -1) * (1.0 + 0.05 * rng.uniform(-1, 1, (cfg.ncell, 1)))),
+               precision) for f in W.asym_state(cfg)]
+    U0 = fluid_targets(cfg, orc, f0, 411)
+    r = AbiRunner(cfg, f0, fluid=np.stack(U0))
+    g = oracle_grid(orc, cfg)
+    for k, sp in enumerate(cfg.species):
+        s = oracle_species(orc, sp)
+        vmom = r.mom()
+        abi.moments(r.ctx, k, vmom)
+        thv = r.torch.zeros((cfg.ncell, 10), dtype=r.torch.float64, device=r.dev)
+        thf = r.torch.zeros_like(thv)
+        abi.moment_fit(r.ctx, k, vmom, False, thv, thf, r.mom())
+        r.sync()
+        ref_f = f0[k].copy()
+        ref_U = U0[k].copy()
+        st = orc.moment_fit(ref_f, g, s, ref_U, cfg.fit_tol, cfg.fit_max_iter)
+        got = r.f_np(k)
+        tol = (1e-10 if precision == 64 else 2e-5) * ref_f.max()
+        assert np.abs(got - ref_f).max() <= tol, (np.abs(got - ref_f).max(), tol)
+        vm = vmom.cpu().numpy()
+        for c in range(0, cfg.ncell, 5):
+            th, it, stt = orc.maxent_fit(vm[c, :10], s, 3, cfg.fit_tol, cfg.fit_max_iter)
+            if stt == 0:
+                np.testing.assert_allclose(thv[c].cpu().numpy(), th, rtol=1e-8, atol=1e-12 * abs(th).max())
+        stats = abi.vl_read_stats(r.ctx)
+        assert stats[1] == st[1] and stats[3] == 0, (stats, st)
+        assert stats[4] > 0 and stats[6] == 0, stats  # every evaluation on the fast path
+        abi.vl_reset_stats(r.ctx)
+    r.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("bc_y", [1, 0])
 def test_fluid_step_matches_oracle(gpu, orc, bc_y, precision):
     """FP64 mode: same arithmetic up to rounding order -> 1e-11. FP32 mode:
