@@ -203,10 +203,15 @@ __global__ void __launch_bounds__(kT) mlp_infer_kernel(MlpInferArgs a) {
                 valid = fit_inputs(tg, a.vmin, a.dv, a.vmax, x);
             }
         }
+        // a fit whose standardised inputs lie outside the training data
+        // (beyond kMaxInputSd standard deviations) gets no warm start
+        bool seen = true;
         for (int q = 0; q < 16; ++q) {
             const float v = (valid && q < kIn) ? (x[q] - snorm[kOffXm + q]) / snorm[kOffXs + q] : 0.f;
+            seen = seen && fabsf(v) <= kMaxInputSd;
             put_bf16(sX, tc::kmajor_offset(t, q, kT), v);
         }
+        if (a.mode == 0) valid = valid && seen;
         // layer 1: Z1 (TMEM columns 0..127)
         st.run([&] { tc::gemm_issue(tmem, sX, sW1, kHid, 16, false); });
         for (int c = 0; c < kHid; c += 16) {
@@ -226,6 +231,10 @@ __global__ void __launch_bounds__(kT) mlp_infer_kernel(MlpInferArgs a) {
         {
             float v[16];
             tc::tmem_ld16(tc::tmem_at(tmem, lane0, 0), v);
+            // ... and so does one whose standardised prediction leaves the
+            // range of the training targets
+            if (a.mode == 0)
+                for (int o = 0; o < kOut; ++o) valid = valid && fabsf(v[o] + sb3[o]) <= kMaxOutputSd;
             if (fit < a.nfit)
                 for (int o = 0; o < kOut; ++o)
                     a.y[fit * kOut + o] =

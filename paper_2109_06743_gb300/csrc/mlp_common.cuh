@@ -45,6 +45,11 @@ constexpr int kOffB3 = kOffW3 + kOut * kHid;
 constexpr int kNParam = kOffB3 + kOut;
 constexpr int kFirstTrained = kOffW1;  // normalisation constants are not trained
 constexpr double kMinScale = 1e-6;    // smallest output scale s_k
+// Out-of-distribution guard of the warm start (fits from targets only): a fit
+// whose standardised inputs lie beyond kMaxInputSd, or whose standardised
+// prediction lies beyond kMaxOutputSd, starts cold (the network has not seen
+// such cells; a prediction far off sends Newton through slow evaluations).
+constexpr float kMaxInputSd = 4.f, kMaxOutputSd = 6.f;
 
 // Inputs of one fit from its targets t = (n, nu_x, nu_y, nu_z, E2_xx, E2_xy,
 // E2_xz, E2_yy, E2_yz, E2_zz); false for targets the fit rejects.

@@ -5,9 +5,11 @@ Every ``--every`` steps it prints one JSON line with the time, the energy
 partition (kinetic+thermal of each species, electric, magnetic; Sec. 3.2's
 energy accounting), the total-energy drift, each species' mass and the
 reconnected flux on the X line (GEM diagnostic, Sec. 3.3) with the
-reconnection rate since the previous line; the steps are FP32 f with the
-moment fit (Algorithm 1), warm-started by a network trained on a smaller run
-of the same velocity grid unless ``--no-mlp``."""
+reconnection rate since the previous line, the step time and the Newton
+iterations per fit; the steps are FP32 f with the moment fit (Algorithm 1),
+warm-started by a network trained on a smaller run of the same velocity grid
+unless ``--no-mlp``, and with ``--retrain-every K`` retrained on the run's
+own fits every K steps."""
 import argparse
 import json
 import sys
@@ -33,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--retrain-every", type=int, default=0,
+                    help="retrain the warm-start network on the run's own fits every this many steps (0: never)")
     ap.add_argument("--out", default=None, help="also write the lines to this file")
     args = ap.parse_args(argv)
     build.build()
@@ -58,17 +62,34 @@ def main(argv=None):
         print(json.dumps(line), flush=True)
         if out:
             out.write(json.dumps(line) + "\n")
+    nfit = 2 * cfg.ncell * len(cfg.species)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    st_prev, k_prev = np.array(sim.stats(), dtype=np.float64), 0
+    retrains = []
     for k in range(1, args.steps + 1):
-        sim.step(use_mlp=mlp is not None)
+        if mlp is not None and args.retrain_every > 0 and k % args.retrain_every == 0:
+            from .warmstart import retrain
+            retrains.append(retrain(sim))  # this step runs with the harvest on
+        else:
+            sim.step(use_mlp=mlp is not None)
         if k % args.every == 0 or k == args.steps:
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev1.record(sim.stream)
             e, m, psi = diagnostics(sim, cfg, yl)
             t = k * cfg.dt
-            st = sim.stats()
+            st = np.array(sim.stats(), dtype=np.float64)
+            d, nk = st - st_prev, k - k_prev
             line = {"step": k, "t": t, "energy": e, "energy_fraction": [x / sum(e) for x in e],
                     "energy_drift": sum(e) / E0 - 1.0, "mass_rel_change": [a / b - 1.0 for a, b in zip(m, m0)],
                     "reconnected_flux": psi, "reconnection_rate": (psi - psi_prev) / (t - t_prev),
-                    "newton_fallbacks": int(st[1]), "wall_s": time.perf_counter() - wall}
-            psi_prev, t_prev = psi, t
+                    "ms_per_step": ev0.elapsed_time(ev1) / nk,
+                    "newton_iterations_per_fit": d[0] / (nfit * nk), "slow_evaluations_per_fit": d[6] / (nfit * nk),
+                    "newton_fallbacks": int(st[1]), "clipped_cells_in_interval": int(d[2]), "retrains": len(retrains),
+                    "wall_s": time.perf_counter() - wall}
+            psi_prev, t_prev, st_prev, k_prev = psi, t, st, k
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(sim.stream)
             print(json.dumps(line), flush=True)
             if out:
                 out.write(json.dumps(line) + "\n")

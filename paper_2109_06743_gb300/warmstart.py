@@ -45,3 +45,26 @@ def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=409
             "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
             "harvest_seconds": t1 - t0, "train_seconds": t2 - t1}
     return w, info
+
+
+def retrain(sim, train_steps=1500, batch=4096, lr=2e-3, seed=2109, use_mlp=True):
+    """Retrain the warm-start network of a running simulation on the fits of
+    its next step (one step is run with the harvest on): the network is
+    re-initialised, standardised on the new samples and trained, so that
+    it follows the cells' moments as the run leaves the states it was
+    trained on. Returns a summary (sample count, last loss, seconds)."""
+    cfg = sim.cfg
+    t0 = time.perf_counter()
+    cap = 4 * cfg.ncell
+    buf = torch.zeros((cap, abi.MLP_SAMPLE), dtype=torch.float32, device=sim.dev)
+    abi.mlp_set_harvest(sim.ctx, buf, cap, sim.stream)
+    sim.step(use_mlp=use_mlp)
+    n = abi.mlp_harvest_count(sim.ctx, sim.stream)
+    abi.mlp_set_harvest(sim.ctx, None, 0, sim.stream)
+    abi.mlp_init(sim.ctx, seed)
+    abi.mlp_normalize(sim.ctx, buf, n, sim.stream)
+    losses = abi.mlp_train(sim.ctx, buf, n, train_steps, batch=batch, lr=lr, seed=seed + 1, record_loss=True,
+                           stream=sim.stream)
+    torch.cuda.synchronize()
+    del buf
+    return {"samples": int(n), "loss_last": float(np.mean(losses[-20:])), "seconds": time.perf_counter() - t0}
