@@ -182,6 +182,19 @@ vl_status moment_fit_solve(vl_ctx* ctx, int species, const double* vmom, int use
 vl_status moment_fit_exchange(vl_ctx* ctx, int species, const double* vmom,
                               double* mom_out, vl_stream_t stream);
 
+/* Selects how the 2D3V Newton fits of this species (Sec. 2.2, Algorithm 1's
+ * moment fitting) evaluate a discrete Maxwellian whose values span more than
+ * the float range over the velocity block, i.e. one that is narrow against
+ * a velocity box sized for a hotter population (values falling below e^-80
+ * of the peak towards the box's corners). wide = 0 (the default): one FP64
+ * exponential per velocity cell for such blocks, and the fit kernel holds
+ * only the common evaluation. wide = 1: a fit kernel that also holds the
+ * centre-out double-float recurrences, which evaluate such blocks at the
+ * common evaluation's speed. The fitted Maxwellians agree to rounding either
+ * way. Takes effect from the next moment_fit(_solve) of the species; host
+ * only, no launch. VL_EINVAL for a bad species. */
+vl_status moment_fit_wide(vl_ctx* ctx, int species, int wide);
+
 /* One SSP-RK3 step (Shu-Osher 1988) of the ten-moment equations of Sec. 2.1
  * for every species with CWENO fluxes (Kurganov-Levy 2000). The third moments
  * come from mom_t[s] (stage 1), mom_t1[s] (stage 2) and their average

@@ -18,7 +18,7 @@ NSTATS = 9  # VL_NSTATS
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
-            "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "fluid_step",
+            "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "moment_fit_wide", "fluid_step",
             "fluid_step_closure", "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
             "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
             "mlp_grad"]
@@ -220,6 +220,10 @@ def moment_fit_solve(ctx, species, vmom, use_mlp=False, theta_v=None, theta_f=No
 
 def moment_fit_exchange(ctx, species, vmom, mom_out=None, stream=None):
     _check(ctx, lib().moment_fit_exchange(ctx, species, ptr(vmom), ptr(mom_out), stream_handle(stream)))
+
+
+def moment_fit_wide(ctx, species, wide):
+    _check(ctx, lib().moment_fit_wide(ctx, species, int(bool(wide))))
 
 
 def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):

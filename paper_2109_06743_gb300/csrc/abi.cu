@@ -34,6 +34,7 @@ struct vl_ctx {
     int adam_step;
     float* harvest;
     long long harvest_cap;
+    bool fit_wide[VL_MAX_SPECIES];  // moment_fit_wide
     char err[512];
 };
 
@@ -457,6 +458,13 @@ vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
     return cuda_check(ctx, vl::launch_moments(a, d.nvdim, d.precision, (cudaStream_t)stream), "moments");
 }
 
+vl_status moment_fit_wide(vl_ctx* ctx, int s, int wide) {
+    if (!ctx) return VL_EINVAL;
+    if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species out of range");
+    ctx->fit_wide[s] = wide != 0;
+    return VL_OK;
+}
+
 vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
                            vl_stream_t stream) {
     vl_status st = check_species(ctx, s);
@@ -483,6 +491,7 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     for (int q = 0; q < 3; ++q) a.vmax[q] = a.vmin[q] + a.dv[q] * (d.nvdim == 3 || q == 0 ? d.nv[s][q] : 1);
     a.tol = d.fit_tol;
     a.max_iter = d.fit_max_iter;
+    a.wide = ctx->fit_wide[s] ? 1 : 0;
     cudaStream_t cs = (cudaStream_t)stream;
     if (use_mlp) {
         vl::MlpInferArgs m;

@@ -123,6 +123,7 @@ struct FitArgs {
     double vmin[3], dv[3], vmax[3];
     double tol;
     int max_iter;
+    int wide;               // 1: the fit kernel with the centre-out evaluation (moment_fit_wide)
 };
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
 

@@ -283,15 +283,16 @@ def test_moment_fit_matches_oracle(gpu, orc, precision, nv):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-@pytest.mark.parametrize("nv", [12, 16])
-def test_moment_fit_of_narrow_maxwellians_stays_on_the_fast_path(gpu, orc, precision, nv):
+@pytest.mark.parametrize("nv,wide", [(12, 1), (16, 1), (12, 0)])
+def test_moment_fit_of_narrow_maxwellians(gpu, orc, precision, nv, wide):
     """Cells of the asymmetric sheet: the velocity boxes are sized for the
     hot side, so on the dense cold side a Maxwellian falls by e^-37 per axis
     towards the box faces and by more than e^-100 into the corners, beyond
-    the float range. The centre-out recurrences of the fit still evaluate
-    every block on the fast path (the counter of FP64-exponential
-    evaluations stays 0), and the fit equals the oracle's as in the test
-    above."""
+    the float range. With the wide fit kernel (moment_fit_wide) the
+    centre-out recurrences evaluate every block on the fast path (the
+    counter of FP64-exponential evaluations stays 0); without it those
+    blocks take the FP64 slow path. Either way the fit equals the oracle's
+    as in the test above."""
     from gpu_util import AbiRunner
     from paper_2109_06743_gb300 import abi
     cfg = W.asym_sheet(nx=3, ny=16, nv=nv, lx=0.6, ly=6.4, precision=precision)
@@ -309,6 +310,7 @@ def test_moment_fit_of_narrow_maxwellians_stays_on_the_fast_path(gpu, orc, preci
     g = oracle_grid(orc, cfg)
     for k, sp in enumerate(cfg.species):
         s = oracle_species(orc, sp)
+        abi.moment_fit_wide(r.ctx, k, wide)
         vmom = r.mom()
         abi.moments(r.ctx, k, vmom)
         thv = r.torch.zeros((cfg.ncell, 10), dtype=r.torch.float64, device=r.dev)
@@ -328,7 +330,10 @@ def test_moment_fit_of_narrow_maxwellians_stays_on_the_fast_path(gpu, orc, preci
                 np.testing.assert_allclose(thv[c].cpu().numpy(), th, rtol=1e-8, atol=1e-12 * abs(th).max())
         stats = abi.vl_read_stats(r.ctx)
         assert stats[1] == st[1] and stats[3] == 0, (stats, st)
-        assert stats[4] > 0 and stats[6] == 0, stats  # every evaluation on the fast path
+        if wide:
+            assert stats[4] > 0 and stats[6] == 0, stats  # every evaluation on the fast path
+        else:
+            assert stats[6] > 0, stats  # the blocks beyond the float range took the slow path
         abi.vl_reset_stats(r.ctx)
     r.close()
 

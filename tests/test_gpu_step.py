@@ -52,6 +52,7 @@ def test_fp64_steps_match_oracle(gpu, orc, kind):
         f, yee = W.wave2d_state(cfg), W.wave2d_yee(cfg)
     cfg.fit_tol = 1e-12
     ost, sim = run_both(cfg, f, yee, 3)
+    assert sim.wide == [False, False]  # boxes of +-5 thermal speeds: the common fit kernel
     for k in range(2):
         ref = ost.f[k]
         got = sim.f_host(k)
