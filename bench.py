@@ -288,6 +288,40 @@ def cpu_baseline(name, steps=1, sample=(32, 16)):
                           steps, cfg.kind, cfg.nx, cfg.ny, nv, cfg.phase_cells(), el)}
 
 
+def _oracle_sample(name, sample, steps):
+    """One process of the all-cores oracle figure: the sample run, timed."""
+    import numpy as np
+
+    from oracle.step import OracleState
+    cfg = make_cfg(name, precision=64, sub=sample)
+    st = OracleState(cfg, initial_state(cfg, np.float64), None, initial_yee(cfg))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.step(cfg.dt)
+    return cfg.phase_cells() * steps, time.perf_counter() - t0
+
+
+def cpu_all_cores(name, sample=(32, 16), steps=1):
+    """The oracle as it stands on every host core: one independent sample run
+    per core, each in its own spawned process (the oracle itself is
+    single-threaded); aggregate rate = all processes' cells over the slowest
+    process's time."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import platform
+
+    import oracle
+    oracle.build()
+    n = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_sample, [name] * n, [sample] * n, [steps] * n))
+    cells = sum(c for c, _ in res)
+    slow = max(t for _, t in res)
+    return {"value": cells / slow, "unit": UNIT, "cores": n, "kind": "oracle", "machine": platform.machine(),
+            "sample": "%d processes, each %d oracle step(s) of the %dx%d subdomain (same dx, dv, dt as the "
+                      "workload), FP64; slowest process %.1f s" % (n, steps, sample[0], sample[1], slow)}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -319,6 +353,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form timed for comparison")
     ap.add_argument("--no-mlp", action="store_true", help="cold-started fits only (no warm-start network)")
+    ap.add_argument("--train-from", default=None, choices=sorted(WORKLOADS),
+                    help="workload whose fits train the warm-start network (default: the same velocity grid)")
+    ap.add_argument("--harvest-steps", type=int, default=24, help="cold-started steps harvested for training")
+    ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle figure")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -347,7 +385,9 @@ def main():
     abi.lib()
 
     device = "cuda:%d" % local
-    mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(TRAIN_FROM[args.workload], device)
+    train_from = args.train_from or TRAIN_FROM[args.workload]
+    mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(train_from, device,
+                                                                         harvest_steps=args.harvest_steps)
     use_mlp = mlp_w is not None
     cfg = make_cfg(args.workload, precision=32)
     f0 = initial_state(cfg, np.float32)
@@ -469,8 +509,7 @@ def main():
     if use_mlp:
         mlp_info.update({"newton_iterations_per_fit": fit_iters, "newton_fallbacks_per_fit": stats[1] / nfits,
                          "cold_start": cold,
-                         "applied_to": args.workload + " (same %d^3-per-species velocity grid)" % cfg.species[0].nv[0]
-                         if TRAIN_FROM[args.workload] != args.workload else args.workload})
+                         "applied_to": args.workload + " (%d^3 velocity cells per species)" % cfg.species[0].nv[0]})
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -499,6 +538,8 @@ def main():
     if rank != 0:
         return 0
     acc, cb = (None, None) if args.no_cpu else subdomain_accuracy(args.workload, mlp_w, device)
+    if cb is not None and not args.no_all_cores:
+        cb["all_cores"] = cpu_all_cores(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
