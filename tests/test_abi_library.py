@@ -65,3 +65,9 @@ def test_workspace_sizing_and_validation_on_host(lib):
     bad.vmin[0][1] = bad.vmin[0][1] * 0.5  # walls need a box symmetric in v_y
     assert abi.vlasov_work_bytes(bad) == 0
     assert isinstance(lib.vl_last_error(None), bytes)
+
+
+def test_host_only_calls_reject_a_missing_context(lib):
+    """moment_fit_wide is host-only: without a context it returns VL_EINVAL
+    (1) and launches nothing."""
+    assert lib.moment_fit_wide(None, 0, 1) == 1
