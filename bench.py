@@ -115,11 +115,12 @@ class ClockSampler:
 # operation.
 OPS_MOMENT_EVAL = 46
 OPS_GRAM_EVAL = 7
-# DRAM bytes per cell of one fit launch (one species) from the ncu capture of
-# newton_kernel<16> on the 256 x 128 x 16^3 case with the warm start
-# (11.66 MB read + 19.85 MB written for 32768 cells: targets, coefficients,
-# status and the kernel's local memory); None once the kernel has changed.
-NEWTON_DRAM_BYTES_PER_CELL = (11.66e6 + 19.85e6) / 32768
+# DRAM bytes per cell of one fit launch (one species), by velocity grid, from
+# the ncu captures of the warm-started 256 x 128 runs (32768 cells: targets,
+# coefficients, status and the kernel's local memory): newton_kernel<16, 0>
+# on the Harris sheet 11.37 MB read + 20.49 MB written, newton_kernel<12, 1>
+# on the asymmetric sheet 12.54 + 49.85 MB; None for grids not captured.
+NEWTON_DRAM_BYTES_PER_CELL = {16: (11.365e6 + 20.491e6) / 32768, 12: (12.545e6 + 49.848e6) / 32768}
 
 
 def alu_peak_tops():
@@ -143,9 +144,8 @@ def newton_roofline(cfg, stats, fit_ms, launches):
     ops = (OPS_MOMENT_EVAL * (stats[4] + stats[6]) + OPS_GRAM_EVAL * (stats[5] + stats[7])) * n3
     achieved = ops / (fit_ms / 1e3) / 1e12
     peak = alu_peak_tops()
-    traffic = None
-    if NEWTON_DRAM_BYTES_PER_CELL is not None:
-        traffic = NEWTON_DRAM_BYTES_PER_CELL * cfg.ncell
+    per_cell = NEWTON_DRAM_BYTES_PER_CELL.get(cfg.species[0].nv[0])
+    traffic = None if per_cell is None else per_cell * cfg.ncell
     return {"kernel": "fit_solve (newton_kernel)", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Tops/s (FP32 pipe)", "frac": achieved / peak, "traffic": traffic,
             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
