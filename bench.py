@@ -288,6 +288,124 @@ def cpu_baseline(name, steps=1, sample=(32, 16)):
                           steps, cfg.kind, cfg.nx, cfg.ny, nv, cfg.phase_cells(), el)}
 
 
+LANDAU = "landau_64_v32"
+
+
+def run_landau(args, rank):
+    """Config 1's line: 1D1V linear Landau damping (Sec. 3.1), 64 x 32 cells,
+    FP64, the whole Algorithm 1 step (Strang x/2, v, x/2, Poisson, fluid,
+    fit) per step. The workload fits in L2 and its kernels take microseconds,
+    so the K timed steps are captured once in a CUDA graph and replayed (the
+    step-by-step launch from Python is reported beside it); the oracle is
+    timed on the same steps of the same workload and compared with it."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle.step import OracleState
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300 import build as B
+    from paper_2109_06743_gb300 import workloads as W
+    from paper_2109_06743_gb300.driver import Simulation
+    if rank != 0:
+        return 0
+    B.build()
+    abi.lib()
+    oracle.build()
+    cfg = W.landau()
+    f0 = W.landau_state(cfg)
+    sim = Simulation(cfg, f0, stream=torch.cuda.Stream())
+    stream = sim.stream
+    cells = cfg.phase_cells()
+    for _ in range(args.warmup):
+        sim.step()
+    torch.cuda.synchronize()
+    # launched step by step from Python (host-bound: ~16 launches per step)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        sim.step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    eager = a.elapsed_time(b) / 1e3
+    # the timed form: the K steps captured once in a CUDA graph and replayed
+    l0 = abi.vl_launch_count()
+    graph = sim.graph(args.steps)
+    launches = abi.vl_launch_count() - l0
+    with torch.cuda.stream(stream):  # a graph replays on the current stream
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    el = a.elapsed_time(b) / 1e3
+    # end to end: f from and back to pinned host memory every step
+    host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
+    for h, f in zip(host, sim.f):
+        h.copy_(f)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.host_streams_after(e0)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            sim.step_through_host(host)
+        sim.wait_host()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    et = e0.elapsed_time(e1) / 1e3
+    nbytes = sum(f.numel() * f.element_size() for f in sim.f)
+    sim.close()
+    # the same number of steps of the oracle from the same f, against a
+    # fresh GPU run of those steps
+    g = Simulation(cfg, f0)
+    ost = OracleState(cfg, f0)
+    E0g, E0o = g.total_energy(), ost.total_energy()
+    n = args.warmup + args.steps
+    t0 = time.perf_counter()
+    for _ in range(n):
+        ost.step(cfg.dt)
+    t_or = time.perf_counter() - t0
+    for _ in range(n):
+        g.step()
+    diff = float(np.abs(g.f_host(0) - ost.f[0]).max() / ost.f[0].max())
+    acc = {"steps": n, "f_max_rel_error": diff,
+           "mass_rel_change_gpu": float(g.f_host(0).sum() / f0[0].sum() - 1.0),
+           "energy_drift_gpu": (g.total_energy() - E0g) / E0g, "energy_drift_oracle": (ost.total_energy() - E0o) / E0o}
+    g.close()
+    peak, peak_kind = peaks()
+    # algorithmic bytes per step: f read and written by the two half sweeps in
+    # x, the velocity sweep and the exchange (8 B each way in FP64)
+    step_bytes = 4 * 16 * cells
+    line = {"metric": METRIC, "value": cells * args.steps / el, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": LANDAU, "grid": [cfg.nx, cfg.species[0].nv[0]], "species": 1,
+                       "phase_cells_per_gpu": cells, "precision": "f64", "splitting": "strang x/2, v, x/2",
+                       "l2": "the workload fits in L2 (%d KB of f): launch-latency bound" % (8 * cells // 1024),
+                       "parallelism": "single"},
+            "roofline": {"kernel": "whole step (L2-resident)", "bound": "hbm",
+                         "achieved": step_bytes / (el / args.steps) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": step_bytes / (el / args.steps) / 1e9 / peak, "traffic": None,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": step_bytes},
+            "accuracy_vs_fp64_oracle": acc,
+            "cpu_baseline": {"value": cells * n / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "the whole workload, %d oracle steps, FP64, one host core, %.2f s" % (n, t_or)},
+            "e2e": {"value": cells * args.steps / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": args.steps},
+            "gpu_launches": launches, "clocks": clk,
+            "launched_from_python": {"value": cells * args.steps / eager, "unit": UNIT,
+                                     "ms_per_step": 1e3 * eager / args.steps}}
+    print(json.dumps(line))
+    return 0
+
+
 def _oracle_sample(name, sample, steps):
     """One process of the all-cores oracle figure: the sample run, timed."""
     import numpy as np
@@ -330,12 +448,25 @@ def run_reference(args, rank):
     oracle.build()
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; warm-up steps are not needed
-    cb = cpu_baseline(args.workload, steps=args.steps, sample=(16, 8))
+    if args.workload == LANDAU:
+        from oracle.step import OracleState
+        from paper_2109_06743_gb300 import workloads as W
+        cfg = W.landau()
+        st = OracleState(cfg, W.landau_state(cfg))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st.step(cfg.dt)
+        el = time.perf_counter() - t0
+        cb = {"value": cfg.phase_cells() * args.steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": "the whole workload, %d oracle steps, FP64, one host core, %.2f s" % (args.steps, el)}
+    else:
+        cb = cpu_baseline(args.workload, steps=args.steps, sample=(16, 8))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "ms_per_step": None,
-            "config": {"workload": args.workload + " (oracle sample: 16x8 spatial subdomain)"},
+            "config": {"workload": args.workload + (" (the whole workload)" if args.workload == LANDAU
+                                                    else " (oracle sample: 16x8 spatial subdomain)")},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -348,7 +479,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="harris_512x256_v16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="harris_512x256_v16", choices=sorted(WORKLOADS) + [LANDAU])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form timed for comparison")
@@ -364,6 +495,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == LANDAU:
+        return run_landau(args, rank)
 
     import numpy as np
     import torch

@@ -188,6 +188,28 @@ class Simulation:
         mark(None)
         self.time += dt
 
+    def graph(self, steps, use_mlp=False):
+        """A CUDA graph of `steps` time steps on the solver's stream, to be
+        replayed with .replay() (for launch-bound workloads such as the 1D1V
+        runs, whose kernels take a few microseconds each). The stream must be
+        a created stream, not the legacy default one; with the fused x+y
+        sweep `steps` must be even, so that each species' two buffers end
+        where they started. A step must have run before (first-launch
+        set-up); replays do not advance self.time, and a replay runs on the
+        current stream (replay inside `with torch.cuda.stream(sim.stream)`
+        to keep it ordered with the solver's other work)."""
+        torch = self.torch
+        if self.stream == torch.cuda.default_stream(self.dev):
+            raise ValueError("capture needs a created stream (Simulation(..., stream=torch.cuda.Stream()))")
+        if self.fused_xy and steps % 2:
+            raise ValueError("with the fused x+y sweep the captured step count must be even")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            for _ in range(steps):
+                self.step(use_mlp=use_mlp)
+        self.time -= steps * self.cfg.dt
+        return g
+
     # pieces per species of the host copies: the copy in of piece c of the
     # next step follows the copy out of piece c of this one, so the two
     # directions pipeline
