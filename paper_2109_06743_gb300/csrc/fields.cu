@@ -193,21 +193,38 @@ cudaError_t launch_current(double* cur, const double* const* src, const double* 
 }
 
 // 1D periodic Poisson dE/dx = rho: face values by a running sum, zero mean,
-// then cell centres as the average of the two faces. One thread (the 1D1V
-// grids are small).
+// then cell centres as the average of the two faces. One warp: each lane
+// sums a contiguous run of cells, an inclusive scan over the lanes gives each
+// run's starting face value, and the mean is a warp sum.
 __global__ void poisson_kernel(const double* rho, double* eb, int nx, double dx) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc = 0.0, mean = 0.0;
-    for (int i = 0; i < nx; ++i) {
-        acc += dx * rho[i];
-        mean += acc;
+    constexpr unsigned kAll = 0xffffffffu;
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int per = (nx + 31) / 32, lo = min(lane * per, nx), hi = min(lo + per, nx);
+    double loc = 0.0;
+    for (int i = lo; i < hi; ++i) loc += dx * rho[i];
+    double inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(kAll, inc, o);
+        if (lane >= o) inc += t;
     }
-    mean /= nx;
-    double prev = acc - mean;  // face -1/2 equals face nx-1/2 (periodic)
-    acc = 0.0;
-    for (int i = 0; i < nx; ++i) {
+    const double before = inc - loc;  // running sum up to the face below lo
+    const double total = __shfl_sync(kAll, inc, 31);
+    double msum = 0.0, acc = before;
+    for (int i = lo; i < hi; ++i) {
         acc += dx * rho[i];
-        double face = acc - mean;
+        msum += acc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(kAll, msum, o);
+    const double mean = msum / nx;
+    // face -1/2 equals face nx-1/2 (periodic)
+    double prev = (lane == 0 ? total : before) - mean;
+    acc = before;
+    for (int i = lo; i < hi; ++i) {
+        acc += dx * rho[i];
+        const double face = acc - mean;
         eb[(long long)i * 6] = 0.5 * (prev + face);
         prev = face;
     }

@@ -325,9 +325,19 @@ __global__ void __launch_bounds__(ex_threads(N)) exchange_kernel(ExchangeArgs a)
 
 // ------------------------------------------------------------------- 1D1V
 
-// One thread per cell: 3-parameter fits (n, u, Theta) by Newton in FP64 on
-// the natural parameters of exp(e0 + e1 w + e2 w^2), then the exchange.
+// One warp per cell: 3-parameter fits (n, u, Theta) by Newton in FP64 on
+// the natural parameters of exp(e0 + e1 w + e2 w^2), then the exchange. The
+// lanes share the velocity cells of a moment evaluation; the sums are reduced
+// by an xor butterfly, which leaves every lane with the same bits, so the
+// Newton control flow is uniform over the warp.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ int fit1d(const double* target, const FitArgs& a, double* theta, int* iters) {
+    const int lane = threadIdx.x & 31;
     *iters = 0;
     const double n = target[0];
     theta[0] = theta[1] = theta[2] = 0.0;
@@ -339,18 +349,17 @@ __device__ int fit1d(const double* target, const FitArgs& a, double* theta, int*
     double eta[3] = {log(n) - 0.5 * log(2.0 * M_PI) - 0.5 * log(th0), 0.0, -0.5};
     const double T[3] = {n, 0.0, n};
     auto eval = [&](const double* e, double* D, double* G4) {
-        for (int q = 0; q < 3; ++q) D[q] = 0.0;
-        for (int q = 0; q < 5; ++q) G4[q] = 0.0;
-        for (int i = 0; i < a.nv; ++i) {
+        double p5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = lane; i < a.nv; i += 32) {
             double w = w0 + i * h;
-            double M = exp(e[0] + e[1] * w + e[2] * w * w) * a.dv[0];
-            double p = M;
+            double p = exp(e[0] + e[1] * w + e[2] * w * w) * a.dv[0];
             for (int q = 0; q < 5; ++q) {
-                if (q < 3) D[q] += p;
-                G4[q] += p;
+                p5[q] += p;
                 p *= w;
             }
         }
+        for (int q = 0; q < 5; ++q) G4[q] = warp_sum_d(p5[q]);
+        for (int q = 0; q < 3; ++q) D[q] = G4[q];
     };
     double D[3], G4[5];
     eval(eta, D, G4);
@@ -406,8 +415,9 @@ __device__ int fit1d(const double* target, const FitArgs& a, double* theta, int*
 }
 
 __global__ void fit1d_kernel(FitArgs a) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= a.ncell) return;
+    const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (c >= a.ncell) return;  // whole warps leave together
+    const bool lead = (threadIdx.x & 31) == 0;
     double tv[3] = {a.vmom[c * 4], a.vmom[c * 4 + 1], a.vmom[c * 4 + 2]};
     const double nF = a.fluid[c * 3];
     const double scale = nF > 0.0 ? tv[0] / nF : 0.0;
@@ -416,8 +426,11 @@ __global__ void fit1d_kernel(FitArgs a) {
     double th[3];
     int itv, itf;
     int stv = fit1d(tv, a, th, &itv);
-    for (int q = 0; q < 3; ++q) a.coef_v[c * kCoef + q] = th[q];
+    if (lead)
+        for (int q = 0; q < 3; ++q) a.coef_v[c * kCoef + q] = th[q];
     int stf = fit1d(tf, a, th, &itf);
+    __syncwarp();  // every lane has read a.fluid before the lead lane rewrites it
+    if (!lead) return;
     for (int q = 0; q < 3; ++q) {
         a.coef_f[c * kCoef + q] = th[q];
         a.fluid[c * 3 + q] = tf[q];
@@ -430,10 +443,12 @@ __global__ void fit1d_kernel(FitArgs a) {
     if (inv) atomicAdd(&a.counters[CNT_INVALID], inv);
 }
 
+// One warp per cell, lanes over the velocity cells.
 template <typename T>
 __global__ void exchange1d_kernel(ExchangeArgs a) {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= a.ncell) return;
+    const long long c = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (c >= a.ncell) return;  // whole warps leave together
+    const int lane = threadIdx.x & 31;
     T* f = reinterpret_cast<T*>(a.f) + c * a.nv;
     const int stv = a.status[c * 2], stf = a.status[c * 2 + 1];
     if (stv != 2 && stf != 2) {
@@ -441,7 +456,7 @@ __global__ void exchange1d_kernel(ExchangeArgs a) {
         const double* tf = a.coef_f + c * kCoef;
         bool neg = false;
         double sum = 0.0;
-        for (int i = 0; i < a.nv; ++i) {
+        for (int i = lane; i < a.nv; i += 32) {
             double v = a.vmin[0] + (i + 0.5) * a.dv[0];
             double mv = tv[0] / sqrt(2.0 * M_PI * tv[2]) * exp(-0.5 * (v - tv[1]) * (v - tv[1]) / tv[2]);
             double mf = tf[0] / sqrt(2.0 * M_PI * tf[2]) * exp(-0.5 * (v - tf[1]) * (v - tf[1]) / tf[2]);
@@ -450,19 +465,22 @@ __global__ void exchange1d_kernel(ExchangeArgs a) {
             neg |= x < T(0);
             sum += x > T(0) ? (double)x : 0.0;
         }
-        if (neg) {
+        if (__any_sync(0xffffffffu, neg)) {
+            sum = warp_sum_d(sum);
             double sc = sum > 0.0 ? a.vmom[c * 4] / (sum * a.dv[0]) : 0.0;
-            for (int i = 0; i < a.nv; ++i) f[i] = (T)(f[i] > T(0) ? (double)f[i] * sc : 0.0);
-            atomicAdd(&a.counters[CNT_CLIPPED], 1ull);
+            for (int i = lane; i < a.nv; i += 32) f[i] = (T)(f[i] > T(0) ? (double)f[i] * sc : 0.0);
+            if (lane == 0) atomicAdd(&a.counters[CNT_CLIPPED], 1ull);
         }
     }
     if (a.mom_out) {
         double m[4] = {0, 0, 0, 0};
-        for (int q = 0; q < a.nv; ++q) {
+        for (int q = lane; q < a.nv; q += 32) {
             double v = a.vmin[0] + (q + 0.5) * a.dv[0], x = (double)f[q];
             m[0] += x; m[1] += v * x; m[2] += v * v * x; m[3] += v * v * v * x;
         }
-        for (int p = 0; p < 4; ++p) a.mom_out[c * 4 + p] = m[p] * a.dv[0];
+        for (int p = 0; p < 4; ++p) m[p] = warp_sum_d(m[p]);
+        if (lane == 0)
+            for (int p = 0; p < 4; ++p) a.mom_out[c * 4 + p] = m[p] * a.dv[0];
     }
 }
 
@@ -497,7 +515,7 @@ cudaError_t launch_theta(const double* coef, const int* status, int which, doubl
 
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st) {
     if (nvdim == 1) {
-        unsigned grid = (unsigned)((a.ncell + 127) / 128);
+        unsigned grid = (unsigned)((a.ncell + 3) / 4);  // a warp per cell
         fit1d_kernel<<<grid, 128, 0, st>>>(a);
         count_launch();
         return cudaGetLastError();
@@ -527,7 +545,7 @@ static cudaError_t launch_exchange_n(const ExchangeArgs& a, cudaStream_t st) {
 
 cudaError_t launch_exchange(const ExchangeArgs& a, int nvdim, int precision, cudaStream_t st) {
     if (nvdim == 1) {
-        unsigned grid = (unsigned)((a.ncell + 127) / 128);
+        unsigned grid = (unsigned)((a.ncell + 3) / 4);  // a warp per cell
         if (precision == 64) exchange1d_kernel<double><<<grid, 128, 0, st>>>(a);
         else exchange1d_kernel<float><<<grid, 128, 0, st>>>(a);
         count_launch();
