@@ -8,8 +8,8 @@ Tolerances (derived from the arithmetic, stated per test):
 * FP32 kernels: inputs are the same FP32 values on both sides; each PFC
   sweep rounds every cell a handful of times -> 2e-6 max|f| per sweep,
   1e-5 max|f| after the five velocity shears; moments within 1e-5 of the
-  absolute moment scale sum |v^alpha| f dv^3 (the tolerance of the
-  spec precision policy for moments in FP32 mode).
+  absolute moment scale sum |v^alpha| f dv^3 (the FP32-mode moment
+  tolerance).
 """
 import math
 
