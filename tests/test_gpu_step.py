@@ -5,8 +5,8 @@ C-ABI against the FP64 oracle, and the physics pins of Sec. 3.1 on the GPU.
   fluid state and fields after a few steps agree with the oracle to 1e-10
   relative (FP64 throughout; differences are rounding order only).
 * FP32 Harris sheet: f within 2e-5 max|f| after 3 steps, total energy
-  within 1e-6 relative of the oracle's (energy drift parity, north-star
-  tolerance 1e-4).
+  within 1e-6 relative of the oracle's (energy drift parity; the FP32-mode
+  drift tolerance is 1e-4).
 * Linear Landau damping on the GPU path (FP64): damping rate and frequency
   within 1% of the dispersion root, mass to 1e-12, energy to 1e-5, and the
   E(t) history equal to the oracle's to 1e-9.
