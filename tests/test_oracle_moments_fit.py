@@ -175,6 +175,53 @@ def test_fit_1d_agrees_with_scipy_root(orc):
     np.testing.assert_allclose(theta, [root[0], root[1], abs(root[2])], rtol=1e-9, atol=1e-12)
 
 
+def test_fit_3d_is_unique_scipy_from_other_starts(orc):
+    """The discrete ten-moment fit (Sec. 2.2; c4) has one solution: scipy's
+    hybrid root finder on a plain numpy evaluation of the discrete moments of
+    M_theta (its own code path: an explicit sum over the cell centres),
+    started from three different parameter sets, lands on the oracle's
+    Newton solution, for a drifting, anisotropic, correlated Maxwellian on a
+    coarse 8^3 grid where the discrete fit differs from the continuous
+    Maxwellian at the 1e-2 level."""
+    from scipy.optimize import root
+    sp = box(8, 4.0)
+    v = [sp.vcentres(a) for a in range(3)]
+    VZ, VY, VX = np.meshgrid(v[2], v[1], v[0], indexing="ij")
+    V = np.stack([VX, VY, VZ], -1).reshape(-1, 3)
+    dv3 = float(np.prod(sp.dv))
+    n, u = 1.3, np.array([0.3, -0.2, 0.1])
+    Th = np.array([[0.9, 0.2, -0.1], [0.2, 0.7, 0.15], [-0.1, 0.15, 1.1]])
+    T = targets_from(n, u, Th)
+    th, it, st = orc.maxent_fit(T, orc_species(orc, sp), 3, 1e-13, 40)
+    assert st == 0
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+    def unpack(p):
+        m = np.zeros((3, 3))
+        for k, (a, b) in enumerate(pairs):
+            m[a, b] = m[b, a] = p[4 + k]
+        return p[0], p[1:4], m
+
+    def resid(p):
+        nn, uu, tt = unpack(p)
+        w = V - uu
+        q = np.einsum("ia,ab,ib->i", w, np.linalg.inv(tt), w)
+        M = nn * np.exp(-0.5 * q) / math.sqrt((2 * math.pi) ** 3 * np.linalg.det(tt)) * dv3
+        E2 = np.einsum("i,ia,ib->ab", M, V, V)
+        return np.concatenate([[M.sum()], M @ V, [E2[a, b] for a, b in pairs]]) - T
+
+    cont = np.concatenate([[n], u, [Th[a, b] for a, b in pairs]])
+    assert np.abs(th - cont).max() > 1e-3  # the discrete fit is not the continuous Maxwellian
+    for scale in (0.9, 1.1, 1.25):
+        start = cont.copy()
+        start[0] *= scale
+        start[1:4] += 0.1 * (scale - 1.0)
+        start[4:] *= scale
+        sol = root(resid, start, method="hybr", tol=1e-12)
+        assert np.abs(resid(sol.x)).max() < 1e-12 * n, sol.message
+        np.testing.assert_allclose(sol.x, th, rtol=1e-8, atol=1e-11)
+
+
 def test_fit_infeasible_falls_back(orc):
     """A variance below what any grid function with that mean can have (mean
     half-way between two cell centres, Theta << dv^2) cannot be fitted: the

@@ -144,6 +144,58 @@ def test_drifting_maxwellian_rotates_by_boris_angle(orc):
     assert abs(np.linalg.norm(u1) - np.linalg.norm(u0)) < 2e-3
 
 
+def test_maxwellian_at_rest_is_invariant_under_b_and_drifts_with_e_cross_b(orc):
+    """c2's physics pins of the velocity map. (1) E = 0, B along z: an
+    isotropic Maxwellian at rest is invariant up to the scheme's
+    discretisation error: density exact, mean velocity 0 to 1e-12 (mirror
+    symmetries of the shears), and the numerical heating over ten steps
+    vanishes as the grid is refined (measured 11%, 0.5%, 1e-4 at 16^3, 32^3,
+    48^3 with the thermal speed 0.77 on +-6). (2) E = E_y y, B = B_z z: over
+    whole gyration periods the mean velocity averages to the E x B drift
+    E_y / B_z along x (Boris map: the drift is exact and the velocity
+    rotates about it)."""
+    vm, th = 6.0, 0.6
+    g = orc.make_grid(3, 1, 1, 0.0, 1.0, 0.0, 1.0, 0)
+    heat = {}
+    for nv in (16, 32, 48):
+        sp = W.SpeciesCfg("i", 1.0, 1.0, (nv, nv, nv), (-vm,) * 3, (vm,) * 3)
+        s = orc.make_species(sp.q, sp.m, sp.nv, sp.vmin, sp.vmax)
+        v = [sp.vcentres(a) for a in range(3)]
+        VZ, VY, VX = np.meshgrid(v[2], v[1], v[0], indexing="ij")
+        f = np.ascontiguousarray(np.exp(-(VX ** 2 + VY ** 2 + VZ ** 2) / (2 * th)).reshape(1, -1))
+        m0 = orc.moments(f, g, s)[0]
+        EB = np.array([[0, 0, 0, 0, 0, 2.0]], dtype=float)
+        for _ in range(10):
+            orc.advect_velocity(f, g, s, EB, 0.05, 5)
+        m1 = orc.moments(f, g, s)[0]
+        assert abs(m1[0] - m0[0]) <= 1e-13 * m0[0]
+        assert np.abs(m1[1:4] / m1[0]).max() < 1e-12
+        heat[nv] = (m1[4] + m1[7] + m1[9]) / m1[0] / ((m0[4] + m0[7] + m0[9]) / m0[0]) - 1.0
+    assert 0 < heat[48] < 1e-3 and heat[48] < heat[32] / 10 < heat[16] / 100, heat
+    nv = 24
+    sp = W.SpeciesCfg("i", 1.0, 1.0, (nv, nv, nv), (-vm,) * 3, (vm,) * 3)
+    s = orc.make_species(sp.q, sp.m, sp.nv, sp.vmin, sp.vmax)
+    v = [sp.vcentres(a) for a in range(3)]
+    VZ, VY, VX = np.meshgrid(v[2], v[1], v[0], indexing="ij")
+    # E x B: Ey = 0.5, Bz = 2 -> drift 0.25 along x; the Boris rotation
+    # angle per step is 2 atan(Bz dt / 2), so 40 steps of dt = 0.0785...
+    # make whole periods
+    f = np.ascontiguousarray(np.exp(-(VX ** 2 + VY ** 2 + VZ ** 2) / (2 * th)).reshape(1, -1))
+    Ey, Bz = 0.5, 2.0
+    nsteps = 40
+    ang = 2 * math.pi / nsteps
+    dt = 2 * math.tan(ang / 2) / Bz
+    EB = np.array([[0, Ey, 0, 0, 0, Bz]], dtype=float)
+    us = []
+    for _ in range(nsteps):
+        orc.advect_velocity(f, g, s, EB, dt, 5)
+        m = orc.moments(f, g, s)[0]
+        us.append(m[1:4] / m[0])
+    ubar = np.mean(us, axis=0)
+    assert abs(ubar[0] - Ey / Bz) < 5e-3, ubar
+    assert abs(ubar[1]) < 5e-3 and abs(ubar[2]) < 1e-12, ubar
+
+
 def test_velocity_push_1d(orc):
     """1D1V: one zero-flux sweep with c = (q/m) E dt / dv."""
     cfg = W.landau(nx=4, nv=16)
