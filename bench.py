@@ -48,6 +48,29 @@ from paper_2109_06743_gb300.workloads import TRAIN_FROM, initial_state, initial_
 from paper_2109_06743_gb300.workloads import named as make_cfg  # noqa: E402
 
 
+def pin_host_to_gpu(device_index):
+    """Run this process on the host cores local to the GPU (its PCI device's
+    local_cpulist in sysfs), so that the pinned host buffers of the
+    end-to-end leg are first touched, and placed, in the GPU's NUMA node.
+    Returns the core list, or None where sysfs does not say."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device_index)
+        bdf = "%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), p.pci_bus_id, p.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bdf) as fh:
+            spec = fh.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if not cpus or len(cpus) >= (os.cpu_count() or 0):
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except Exception:
+        return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -518,6 +541,7 @@ def main():
     abi.lib()
 
     device = "cuda:%d" % local
+    affinity = pin_host_to_gpu(local)
     train_from = args.train_from or TRAIN_FROM[args.workload]
     mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(train_from, device,
                                                                          harvest_steps=args.harvest_steps)
@@ -683,7 +707,7 @@ def main():
                                 "double-float Newton fit" + ("; BF16 warm-start network" if use_mlp else ""),
                    "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
                        sum(cfg.ncell * s.vblock for s in cfg.species) * 4 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "host_cores": affinity},
         "roofline": roof,
         "phases_ms_per_step": {k: v / args.steps for k, v in sorted(phase_ms.items())},
         "hbm_phases": rows,
