@@ -1,12 +1,13 @@
-"""Parity at the benchmark's full size, in its launch configuration: the
-Harris sheet 512 x 256 x 16^3 per species, FP32, one step's passes issued
+"""Parity at the benchmark's full sizes, in its launch configuration: the
+Harris sheet 512 x 256 x 16^3 and the asymmetric sheet 1024 x 512 x 12^3
+per species (its wide fit kernel), FP32, one step's passes issued
 through the C ABI in the driver's order (fields, fused x+y sweep, velocity
 pass with fused moments, fit, exchange). The oracle computes sampled
 outputs one by one:
 
 * fused x+y sweep: the value at a sampled (y, x, velocity) cell from the
-  oracle's PFC line step along x of the rows y-4 .. y+4 (periodic lines of
-  512 cells) and then along y of those nine values (rows away from the
+  oracle's PFC line step along x of the rows y-4 .. y+4 (whole periodic
+  lines) and then along y of those nine values (rows away from the
   walls), within 4e-6 of max f (two FP32 sweeps); over the whole grid, mass
   is conserved to 1e-6 and f stays non-negative;
 * velocity pass: sampled blocks advected by the oracle with the cell's E and
@@ -36,14 +37,17 @@ def gpu():
     return torch
 
 
-def test_full_size_passes_match_the_oracle_on_samples(gpu, orc):
+@pytest.mark.parametrize("name", ["harris_512x256_v16", "asym_1024x512_v12"])
+def test_full_size_passes_match_the_oracle_on_samples(gpu, orc, name):
     torch = gpu
     from paper_2109_06743_gb300 import abi
     from paper_2109_06743_gb300.driver import Simulation
-    cfg = W.named("harris_512x256_v16", precision=32)
+    cfg = W.named(name, precision=32)
     f0 = W.initial_state(cfg, np.float32)
     sim = Simulation(cfg, f0, None, W.initial_yee(cfg))
-    ctx, s, dt, nv = sim.ctx, sim.stream, cfg.dt, 16
+    del f0
+    assert sim.wide == [cfg.kind == "asym"] * 2
+    ctx, s, dt, nv = sim.ctx, sim.stream, cfg.dt, cfg.species[0].nv[0]
     V = nv ** 3
     rng = np.random.default_rng(2109)
     abi.maxwell_step(ctx, 0.5 * dt, None, s)
