@@ -215,19 +215,21 @@ def fluid_targets(cfg, orc, f_list, seed):
     rng = np.random.default_rng(seed)
     g = oracle_grid(orc, cfg)
     out = []
-    for f, sp in zip(f_list, cfg.species):
-        m = orc.moments(f, g, oracle_species(orc, sp))
-        n = m[:, 0] * (1.0 + 0.01 * rng.uniform(-1, 1, cfg.ncell))
-        u = m[:, 1:4] / m[:, :1] + 0.05 * np.array(sp.dv)[None, :] * rng.uniform(-1, 1, (cfg.ncell, 3))
-        E2 = m[:, 4:10] / m[:, :1]
-        mu = m[:, 1:4] / m[:, :1]
-        thv = E2 - np.stack([mu[:, 0] ** 2, mu[:, 0] * mu[:, 1], mu[:, 0] * mu[:, 2], mu[:, 1] ** 2,
-                             mu[:, 1] * mu[:, 2], mu[:, 2] ** 2], axis=1)
-        thf = thv * (1.0 + 0.02 * rng.uniform(-1, 1, (cfg.ncell, 1)))
-        uu = np.stack([u[:, 0] ** 2, u[:, 0] * u[:, 1], u[:, 0] * u[:, 2], u[:, 1] ** 2, u[:, 1] * u[:, 2],
-                       u[:, 2] ** 2], axis=1)
-        U = np.concatenate([n[:, None], n[:, None] * u, n[:, None] * (thf + uu)], axis=1)
-        out.append(np.ascontiguousarray(U))
+    # empty cells give 0/0: invalid targets, as intended
+    with np.errstate(invalid="ignore"):
+        for f, sp in zip(f_list, cfg.species):
+            m = orc.moments(f, g, oracle_species(orc, sp))
+            n = m[:, 0] * (1.0 + 0.01 * rng.uniform(-1, 1, cfg.ncell))
+            u = m[:, 1:4] / m[:, :1] + 0.05 * np.array(sp.dv)[None, :] * rng.uniform(-1, 1, (cfg.ncell, 3))
+            E2 = m[:, 4:10] / m[:, :1]
+            mu = m[:, 1:4] / m[:, :1]
+            thv = E2 - np.stack([mu[:, 0] ** 2, mu[:, 0] * mu[:, 1], mu[:, 0] * mu[:, 2], mu[:, 1] ** 2,
+                                 mu[:, 1] * mu[:, 2], mu[:, 2] ** 2], axis=1)
+            thf = thv * (1.0 + 0.02 * rng.uniform(-1, 1, (cfg.ncell, 1)))
+            uu = np.stack([u[:, 0] ** 2, u[:, 0] * u[:, 1], u[:, 0] * u[:, 2], u[:, 1] ** 2, u[:, 1] * u[:, 2],
+                           u[:, 2] ** 2], axis=1)
+            U = np.concatenate([n[:, None], n[:, None] * u, n[:, None] * (thf + uu)], axis=1)
+            out.append(np.ascontiguousarray(U))
     return out
 
 
