@@ -97,7 +97,9 @@ class Simulation:
     def wide_species(self):
         """Per species, whether some cell's Maxwellian (from the current
         moments of f) falls by more than WIDE_SPREAD e-folds from its peak to
-        the farthest corner of the velocity box."""
+        the farthest corner of the velocity box; cells whose density is below
+        1e-10 of the species' largest (whose fits are not valid anyway) are
+        left out."""
         torch = self.torch
         out = []
         for sp, m in zip(self.cfg.species, self.mom_t):
@@ -109,7 +111,8 @@ class Simulation:
                     th = (m[:, d] / n - u * u).clamp_min(1e-300)
                     ext = torch.maximum(sp.vmax[a] - u, u - sp.vmin[a])
                     spread = spread + ext * ext / (2.0 * th)
-                big = bool((spread > self.WIDE_SPREAD).any().item())
+                live = m[:, 0] > 1e-10 * m[:, 0].max()
+                big = bool(((spread > self.WIDE_SPREAD) & live).any().item())
             out.append(big)
         return out
 
