@@ -53,7 +53,10 @@ int or_advect_space(double* f, const or_grid* g, const or_species* sp,
 /* Velocity-space advection under (q/m)(E + v x B) over dt at every spatial
  * cell. EB is cell centred, [ncell][6] = Ex Ey Ez Bx By Bz. nshear = 5 uses
  * the exact shear factorisation of the Boris map, 3 the plain x,y,z split.
- * Zero-flux boundaries at the velocity box. In place. */
+ * Zero-flux boundaries at the velocity box. In place.
+ * Pinned: the five shears compose to the Boris map, rest invariance, E x B
+ * drift. Parity unpinned: agreement with the paper's own velocity splitting
+ * (its backsubstitution sweeps are cited, not given). */
 int or_advect_velocity(double* f, const or_grid* g, const or_species* sp,
                        const double* EB, double dt, int nshear);
 
