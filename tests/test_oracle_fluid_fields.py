@@ -191,3 +191,28 @@ def test_poisson_second_order(orc):
         E = orc.poisson_1d(rho, dx)
         errs.append(np.abs(E - np.sin(k * x) / k).max())
     assert errs[0] < 1.5e-2 and math.log2(errs[0] / errs[1]) > 1.9
+
+
+def test_fields_to_centres_is_exact_for_linear_fields(orc):
+    """Reading: each Yee component is averaged from its staggered points to
+    the cell centre by the symmetric 2- or 4-point mean (Bz is already
+    there). A field linear in its position, a + b x + c y, is then exact at
+    every centre away from the periodic wrap in x."""
+    nx, ny, x0, dx, y0, dy = 10, 7, -1.0, 0.3, -0.7, 0.2
+    g = orc.make_grid(3, nx, ny, x0, dx, y0, dy, 1)
+    xs_int, xs_half = x0 + np.arange(nx) * dx, x0 + (np.arange(nx) + 0.5) * dx
+    ys_int, ys_half = y0 + np.arange(ny + 1) * dy, y0 + (np.arange(ny + 1) + 0.5) * dy
+    # positions (x, y) of each plane's points: Ex(i+1/2, j), Ey(i, j+1/2),
+    # Ez(i, j), Bx(i, j+1/2), By(i+1/2, j), Bz(i+1/2, j+1/2)
+    pos = [(xs_half, ys_int), (xs_int, ys_half), (xs_int, ys_int), (xs_int, ys_half), (xs_half, ys_int),
+           (xs_half, ys_half)]
+    coef = [(0.3, 1.1, -0.7), (-0.2, 0.4, 0.9), (1.5, -0.6, 0.25), (0.05, 0.8, -1.2), (0.7, -0.3, 0.6),
+            (-0.4, 0.2, 1.3)]
+    yee = np.zeros((6, ny + 1, nx))
+    for k, ((px, py), (a, b, c)) in enumerate(zip(pos, coef)):
+        yee[k] = a + b * px[None, :] + c * py[:, None]
+    EB = orc.fields_to_centres(np.ascontiguousarray(yee.reshape(-1)), g).reshape(ny, nx, 6)
+    xc, yc = x0 + (np.arange(nx) + 0.5) * dx, y0 + (np.arange(ny) + 0.5) * dy
+    for k, (a, b, c) in enumerate(coef):
+        want = a + b * xc[None, :] + c * yc[:, None]
+        np.testing.assert_allclose(EB[:, 1:nx - 1, k], want[:, 1:nx - 1], rtol=0, atol=1e-13, err_msg=str(k))
