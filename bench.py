@@ -647,7 +647,7 @@ def main():
         barrier_sync()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        ksteps = max(1, min(args.steps, 5))
+        ksteps = max(1, min(args.steps, 10))
         e0.record(stream)
         sim.host_streams_after(e0)
         with torch.cuda.stream(stream):
