@@ -108,6 +108,40 @@ def test_fluid_gyration(orc):
     np.testing.assert_allclose(U[0, 4] + U[0, 7] + U[0, 9], 2.5, atol=1e-9)
 
 
+def test_fluid_acceleration_by_a_uniform_e_field_is_exact(orc):
+    """Eqs. 2-4 with B = 0 and a uniform E on a uniform state: the fluxes
+    vanish and the sources give d(nu)/dt = (q/m) n E and
+    d(E2_ab)/dt = (q/m)(nu_a E_b + nu_b E_a), so nu is linear and E2 quadratic
+    in t, which SSP-RK3 integrates exactly. One step equals the closed form
+    n u + (q/m) n E t, E2 + (q/m)(nu E + E nu) t + (q/m)^2 n E E t^2 to
+    rounding (pins the signs, the factor q/m and the symmetrisation of the
+    E2 source); the work done, (m/2) d tr(E2), is q t E . (nu + (q/m) n E t/2)."""
+    g = orc.make_grid(3, 3, 2, 0.0, 1.0, 0.0, 1.0, 0)
+    n, u = 1.4, np.array([0.3, -0.5, 0.2])
+    th = np.array([[0.6, 0.1, 0.0], [0.1, 0.5, -0.05], [0.0, -0.05, 0.7]])
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    U0 = np.array([n, *(n * u)] + [n * (th[a, b] + u[a] * u[b]) for a, b in pairs])
+    U = np.tile(U0, (6, 1))
+    E = np.array([0.7, -0.4, 1.1])
+    EB = np.zeros((6, 6))
+    EB[:, :3] = E
+    q, m = -2.0, 0.5
+    qm = q / m
+    sp = orc.make_species(q, m, (4, 4, 4), (-1, -1, -1), (1, 1, 1))
+    Q = np.zeros((6, 10))
+    t = 0.03
+    orc.fluid_step(U, g, sp, Q, Q, Q, EB, t)
+    nu = n * u
+    nu_t = nu + qm * n * E * t
+    E2 = n * (th + np.outer(u, u))
+    E2_t = E2 + qm * (np.outer(nu, E) + np.outer(E, nu)) * t + qm * qm * n * np.outer(E, E) * t * t
+    want = np.array([n, *nu_t] + [E2_t[a, b] for a, b in pairs])
+    for c in range(6):
+        np.testing.assert_allclose(U[c], want, rtol=0, atol=1e-14)
+    work = 0.5 * m * (np.trace(E2_t) - np.trace(E2))
+    assert abs(work - q * t * E @ (nu + 0.5 * qm * n * E * t)) < 1e-14
+
+
 def _mode_test(orc, nx, ny, comp_e, comp_b, along):
     c = 3.0
     g = orc.make_grid(3, nx, ny, 0.0, 0.25, 0.0, 0.25, 0)
