@@ -66,3 +66,15 @@ def test_reference_arm_prints_one_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.slow
+def test_all_cores_oracle_figure():
+    """The all-cores oracle figure: one spawned process per host core, each
+    timing the same bounded sample; the aggregate counts every process's
+    cells over the slowest process's time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_all_cores("harris_512x256_v16", sample=(8, 4))
+    assert r["kind"] == "oracle" and r["cores"] == (os.cpu_count() or 1) and r["value"] > 0
+    assert "8x4" in r["sample"]
