@@ -148,20 +148,23 @@ def harris(nx=128, ny=64, nv=20, lx=25.6, ly=12.8, mass_ratio=25.0, lam=0.5, nb=
     cfg = Config("harris_2d3v_%dx%d_v%d" % (nx, ny, nv), 3, nx, ny, -lx / 2, lx, -ly / 2, ly, 1,
                  species, dt, steps, c=c, precision=precision)
     cfg.lam, cfg.nb, cfg.psi0, cfg.kind = lam, nb, psi0, "harris"
+    # wavelengths of the psi perturbation: the sheet's own box (a window of a
+    # larger sheet keeps the larger sheet's, see named())
+    cfg.plx, cfg.ply = lx, ly
     return cfg
 
 
 def _harris_Az(cfg, x, y):
     lam, psi0 = cfg.lam, cfg.psi0
-    return lam * np.log(np.cosh(y / lam)) + psi0 * np.cos(2 * math.pi * x / cfg.lx) * np.cos(math.pi * y / cfg.ly)
+    return lam * np.log(np.cosh(y / lam)) + psi0 * np.cos(2 * math.pi * x / cfg.plx) * np.cos(math.pi * y / cfg.ply)
 
 
 def _harris_profiles(cfg, x, y):
     """density n(x,y) and total current j_z(x,y) of the initial sheet"""
     lam = cfg.lam
     n = 1.0 / np.cosh(y / lam) ** 2 + cfg.nb
-    jz = -(1.0 / lam) / np.cosh(y / lam) ** 2 + cfg.psi0 * np.cos(2 * math.pi * x / cfg.lx) * np.cos(
-        math.pi * y / cfg.ly) * ((2 * math.pi / cfg.lx) ** 2 + (math.pi / cfg.ly) ** 2)
+    jz = -(1.0 / lam) / np.cosh(y / lam) ** 2 + cfg.psi0 * np.cos(2 * math.pi * x / cfg.plx) * np.cos(
+        math.pi * y / cfg.ply) * ((2 * math.pi / cfg.plx) ** 2 + (math.pi / cfg.ply) ** 2)
     return n, jz
 
 
@@ -509,13 +512,19 @@ TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "
 
 def named(name, precision=32, sub=None) -> Config:
     """The named workload; with sub = (nx, ny) the central subdomain of it
-    with the same dx, dy, velocity grid and dt."""
+    with the same dx, dy, velocity grid and dt: a window of the workload's
+    initial state (its profiles and perturbation evaluated at the window's
+    cells), periodic in x and with walls in y like the whole sheet."""
     kind, nx, ny, nv, lx, ly = NAMED[name]
+    flx, fly = lx, ly
     if sub is not None:
         lx, ly = lx * sub[0] / nx, ly * sub[1] / ny
         nx, ny = sub
     make = harris if kind == "harris" else asym_sheet
-    return make(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
+    cfg = make(nx=nx, ny=ny, nv=nv, lx=lx, ly=ly, precision=precision)
+    if kind == "harris":
+        cfg.plx, cfg.ply = flx, fly
+    return cfg
 
 
 def initial_state(cfg: Config, dtype=np.float64):
