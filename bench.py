@@ -130,50 +130,82 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# FP32-pipe operations (add, multiply or fused multiply-add: one each) per
-# velocity cell of one evaluation in the double-float Newton fit: moments of
-# degree <= 2 (two double-float products for the recurrence, three
-# compensated accumulations, the index step), plus the FP32 sums of degree
-# <= 4 when the Jacobian is formed in the same pass, counted operation by
+# Work of the Newton fits per velocity cell and evaluation of a discrete
+# Maxwellian, in operations (add, multiply or fused multiply-add: one each).
+# The method's own work (Sec. 2.2's discrete fit): the ten moment sums of
+# degree <= 2 per evaluation, and 25 more sums (degree 3 and 4, the entries
+# of the Gram matrix beyond the moments) when the Jacobian is formed.
+METHOD_OPS_MOMENT = 10
+METHOD_OPS_GRAM = 25
+# What the double-float kernel issues on the FP32 pipe for the same work:
+# two double-float products for the recurrence, three compensated
+# accumulations and the index step (46), plus the FP32 sums of degree <= 4
+# when the Jacobian is formed in the same pass (7), counted operation by
 # operation.
-OPS_MOMENT_EVAL = 46
-OPS_GRAM_EVAL = 7
-# DRAM bytes per cell of one fit launch (one species), by velocity grid, from
-# the ncu captures of the warm-started 256 x 128 runs (32768 cells: targets,
-# coefficients, status and the kernel's local memory): newton_kernel<16, 0>
-# on the Harris sheet 11.37 MB read + 20.49 MB written, newton_kernel<12, 1>
-# on the asymmetric sheet 12.54 + 49.85 MB; None for grids not captured.
-NEWTON_DRAM_BYTES_PER_CELL = {16: (11.365e6 + 20.491e6) / 32768, 12: (12.545e6 + 49.848e6) / 32768}
+ISSUED_OPS_MOMENT_DF = 46
+ISSUED_OPS_GRAM_DF = 7
+# What the FP64 kernel issues on the FP64 pipe: the two products of the
+# recurrence and three accumulations (5), plus two accumulations with the
+# Gram sums (2).
+ISSUED_OPS_MOMENT_64 = 5
+ISSUED_OPS_GRAM_64 = 2
+# DRAM bytes per cell of one fit launch (one species), by kernel and velocity
+# grid, from ncu captures of the current kernels (targets, coefficients,
+# status and the kernel's local memory); a grid not captured gives None.
+NEWTON_DRAM_BYTES_PER_CELL = {}
 
 
-def alu_peak_tops():
-    """FP32-pipe peak from the unit counts and clock: 152 SMs x 128 FP32
-    lanes x the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz)."""
-    mhz = 2070.0
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as fh:
-            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
-    return 152 * 128 * mhz * 1e6 / 1e12
+def measured_alu_peaks(device):
+    """FMA operations per second of this GPU in FP32 and FP64, measured by
+    the library's probe kernel (vl_fma_peak: independent FMA chains timed
+    with CUDA events; no device setting is changed)."""
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    sink = torch.zeros(1, dtype=torch.float64, device=device)
+    p32 = abi.vl_fma_peak(32, sink)
+    p64 = abi.vl_fma_peak(64, sink)
+    return {"fp32_tops": p32 / 1e12, "fp64_tops": p64 / 1e12,
+            "how": "vl_fma_peak: 8 independent FMA chains per thread, 8 x 256-thread blocks per SM, CUDA events, "
+                   "FMA counted as one operation"}
 
 
-def newton_roofline(cfg, stats, fit_ms, launches):
-    """ALU roofline of the Newton fit kernel over the timed region: the
-    algorithmic FP32-pipe operations (device counters of the evaluations x
-    velocity cells x operations per cell) over the kernel's CUDA-event time."""
+def newton_roofline(cfg, stats, fit_ms, launches, alu, fp64=False):
+    """ALU roofline of the Newton fit kernel over the timed region. achieved
+    = the method's operations (device counters of the evaluations x
+    velocity cells x METHOD_OPS_*) over the kernel's CUDA-event time; peak =
+    the measured FMA rate of the pipe the kernel computes on (FP32 for the
+    double-float fit, FP64 for the FP64 fit). The operations the kernel
+    actually issues for that work are reported beside it."""
     if not fit_ms:
         return None
     n3 = cfg.species[0].nv[0] ** 3
-    ops = (OPS_MOMENT_EVAL * (stats[4] + stats[6]) + OPS_GRAM_EVAL * (stats[5] + stats[7])) * n3
-    achieved = ops / (fit_ms / 1e3) / 1e12
-    peak = alu_peak_tops()
-    per_cell = NEWTON_DRAM_BYTES_PER_CELL.get(cfg.species[0].nv[0])
-    traffic = None if per_cell is None else per_cell * cfg.ncell
-    return {"kernel": "fit_solve (newton_kernel)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "Tops/s (FP32 pipe)", "frac": achieved / peak, "traffic": traffic,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
-            "ops_per_launch": ops / max(1, launches),
-            "evaluations": {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7]}}
+    secs = fit_ms / 1e3
+    if fp64:
+        em, eg = stats[10], stats[11]
+        issued = (ISSUED_OPS_MOMENT_64 * em + ISSUED_OPS_GRAM_64 * eg) * n3
+        peak = alu["fp64_tops"]
+        kernel, pipe = "fit_solve (newton64_kernel, FP64)", "FP64"
+        evals = {"moments": em, "gram": eg}
+    else:
+        em, eg = stats[4] + stats[6], stats[5] + stats[7]
+        issued = (ISSUED_OPS_MOMENT_DF * em + ISSUED_OPS_GRAM_DF * eg) * n3
+        peak = alu["fp32_tops"]
+        kernel, pipe = "fit_solve (newton_kernel, double-float on the FP32 pipe)", "FP32"
+        evals = {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7],
+                 "wide_kernel_fits": stats[9]}
+    method = (METHOD_OPS_MOMENT * em + METHOD_OPS_GRAM * eg) * n3
+    achieved = method / secs / 1e12
+    per_cell = NEWTON_DRAM_BYTES_PER_CELL.get((fp64, cfg.species[0].nv[0]))
+    out = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (%s pipe)" % pipe,
+           "frac": achieved / peak, "traffic": None if per_cell is None else per_cell * cfg.ncell,
+           "peak_kind": "measured (vl_fma_peak)",
+           "method_ops_per_launch": method / max(1, launches), "method_frac": achieved / peak,
+           "issued_ops_per_launch": issued / max(1, launches), "issued_frac": issued / secs / 1e12 / peak,
+           "evaluations": evals}
+    if not fp64:
+        out["method_vs_fp64_peak"] = achieved / alu["fp64_tops"]
+    return out
 
 
 def slowest(seconds, dist=None, device="cpu"):
@@ -314,47 +346,43 @@ def cpu_baseline(name, steps=1, sample=(32, 16)):
 LANDAU = "landau_64_v32"
 
 
-def run_landau(args, rank):
-    """Config 1's line: 1D1V linear Landau damping (Sec. 3.1), 64 x 32 cells,
-    FP64, the whole Algorithm 1 step (Strang x/2, v, x/2, Poisson, fluid,
-    fit) per step. The workload fits in L2 and its kernels take microseconds,
-    so the K timed steps are captured once in a CUDA graph and replayed (the
-    step-by-step launch from Python is reported beside it); the oracle is
-    timed on the same steps of the same workload and compared with it."""
+def landau_block(steps, warmup):
+    """Config 1's measurement: 1D1V linear Landau damping (Sec. 3.1), 64 x 32
+    cells, FP64, the whole Algorithm 1 step (Strang x/2, v, x/2, Poisson,
+    fluid, fit) per step. The workload fits in L2 and its kernels take
+    microseconds, so the K timed steps are captured once in a CUDA graph and
+    replayed (the step-by-step launch from Python is reported beside it);
+    the oracle is timed on the same steps of the same workload and compared
+    with it. Returns the fields of a bench line."""
     import numpy as np
     import torch
 
     import oracle
     from oracle.step import OracleState
     from paper_2109_06743_gb300 import abi
-    from paper_2109_06743_gb300 import build as B
     from paper_2109_06743_gb300 import workloads as W
     from paper_2109_06743_gb300.driver import Simulation
-    if rank != 0:
-        return 0
-    B.build()
-    abi.lib()
     oracle.build()
     cfg = W.landau()
     f0 = W.landau_state(cfg)
     sim = Simulation(cfg, f0, stream=torch.cuda.Stream())
     stream = sim.stream
     cells = cfg.phase_cells()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sim.step()
     torch.cuda.synchronize()
     # launched step by step from Python (host-bound: ~16 launches per step)
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         sim.step()
     b.record(stream)
     torch.cuda.synchronize()
     eager = a.elapsed_time(b) / 1e3
     # the timed form: the K steps captured once in a CUDA graph and replayed
     l0 = abi.vl_launch_count()
-    graph = sim.graph(args.steps)
+    graph = sim.graph(steps)
     launches = abi.vl_launch_count() - l0
     with torch.cuda.stream(stream):  # a graph replays on the current stream
         graph.replay()
@@ -377,7 +405,7 @@ def run_landau(args, rank):
     e0.record(stream)
     sim.host_streams_after(e0)
     with torch.cuda.stream(stream):
-        for _ in range(args.steps):
+        for _ in range(steps):
             sim.step_through_host(host)
         sim.wait_host()
     e1.record(stream)
@@ -390,7 +418,7 @@ def run_landau(args, rank):
     g = Simulation(cfg, f0)
     ost = OracleState(cfg, f0)
     E0g, E0o = g.total_energy(), ost.total_energy()
-    n = args.warmup + args.steps
+    n = warmup + steps
     t0 = time.perf_counter()
     for _ in range(n):
         ost.step(cfg.dt)
@@ -406,26 +434,36 @@ def run_landau(args, rank):
     # algorithmic bytes per step: f read and written by the two half sweeps in
     # x, the velocity sweep and the exchange (8 B each way in FP64)
     step_bytes = 4 * 16 * cells
-    line = {"metric": METRIC, "value": cells * args.steps / el, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+    return {"metric": METRIC, "value": cells * steps / el, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": LANDAU, "grid": [cfg.nx, cfg.species[0].nv[0]], "species": 1,
                        "phase_cells_per_gpu": cells, "precision": "f64", "splitting": "strang x/2, v, x/2",
                        "l2": "the workload fits in L2 (%d KB of f): launch-latency bound" % (8 * cells // 1024),
                        "parallelism": "single"},
             "roofline": {"kernel": "whole step (L2-resident)", "bound": "hbm",
-                         "achieved": step_bytes / (el / args.steps) / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": step_bytes / (el / args.steps) / 1e9 / peak, "traffic": None,
+                         "achieved": step_bytes / (el / steps) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": step_bytes / (el / steps) / 1e9 / peak, "traffic": None,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": step_bytes},
             "accuracy_vs_fp64_oracle": acc,
             "cpu_baseline": {"value": cells * n / t_or, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "the whole workload, %d oracle steps, FP64, one host core, %.2f s" % (n, t_or)},
-            "e2e": {"value": cells * args.steps / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes, "steps": args.steps},
+            "e2e": {"value": cells * steps / et, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes, "steps": steps},
             "gpu_launches": launches, "clocks": clk,
-            "launched_from_python": {"value": cells * args.steps / eager, "unit": UNIT,
-                                     "ms_per_step": 1e3 * eager / args.steps}}
-    print(json.dumps(line))
+            "launched_from_python": {"value": cells * steps / eager, "unit": UNIT,
+                                     "ms_per_step": 1e3 * eager / steps}}
+
+
+def run_landau(args, rank):
+    """The Landau workload as the bench line itself (--workload landau_64_v32)."""
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300 import build as B
+    if rank != 0:
+        return 0
+    B.build()
+    abi.lib()
+    print(json.dumps(landau_block(args.steps, args.warmup)))
     return 0
 
 
@@ -496,6 +534,325 @@ def run_reference(args, rank):
     return 0
 
 
+def timed_steps(sim, steps, use_mlp):
+    """K steps on the solver's stream, bracketed by CUDA events, with an event
+    before every phase; returns (seconds, {phase: ms}, {phase: launches},
+    kernels launched by the library)."""
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    stream = sim.stream
+    pending = []
+    cur = {"label": None, "ev": None}
+
+    def mark(label):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        if cur["label"] is not None:
+            pending.append((cur["label"], cur["ev"], ev))
+        cur["label"], cur["ev"] = label, ev
+
+    l0 = abi.vl_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        sim.step(use_mlp=use_mlp, mark=mark)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = abi.vl_launch_count() - l0
+    phase_ms, count = {}, {}
+    for label, e0, e1 in pending:
+        phase_ms[label] = phase_ms.get(label, 0.0) + e0.elapsed_time(e1)
+        count[label] = count.get(label, 0) + 1
+    return t0.elapsed_time(t1) / 1e3, phase_ms, count, launches
+
+
+def hbm_rows(phase_ms, count, per_launch_cells, bytes_per_cell=8):
+    """HBM fraction of each memory-bound pass: algorithmic bytes (f read and
+    written once) per launch over the phase's CUDA-event time per launch."""
+    peak, peak_kind = peaks()
+    rows = {}
+    for ph in ("xy_sweep", "x_sweep", "y_sweep", "v_pass", "fit_exchange"):
+        if ph in phase_ms:
+            avg_s = phase_ms[ph] / count[ph] / 1e3
+            gbs = bytes_per_cell * per_launch_cells / avg_s / 1e9
+            rows[ph] = {"ms_per_launch": avg_s * 1e3, "GBps": gbs, "frac_of_%s_hbm" % peak_kind: gbs / peak}
+    return rows
+
+
+def host_link(host, dev, reps=3):
+    """Pinned host <-> device copy rates with plain cudaMemcpyAsync (torch
+    copy_ of pinned tensors, one stream per direction): host to device
+    alone, device to host alone, and both at once; the roof of the
+    end-to-end leg, which moves f both ways every step."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nbytes = sum(h.numel() * h.element_size() for h in host)
+
+    def run(h2d, d2h):
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(s1)
+            s2.wait_event(e[0])
+            if h2d:
+                with torch.cuda.stream(s1):
+                    for h, d in zip(host, dev):
+                        d.copy_(h, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    for h, d in zip(host, dev):
+                        h.copy_(d, non_blocking=True)
+            e[1].record(s1)
+            e[2].record(s2)
+            s1.wait_event(e[2])
+            e[3].record(s1)
+            torch.cuda.synchronize()
+            t = e[0].elapsed_time(e[3]) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    t_h2d = run(True, False)
+    t_d2h = run(False, True)
+    t_both = run(True, True)
+    return {"bytes_each_way": nbytes, "h2d_GBps": nbytes / t_h2d / 1e9, "d2h_GBps": nbytes / t_d2h / 1e9,
+            "both_directions_GBps_each_way": nbytes / t_both / 1e9,
+            "step_copy_ms_at_roof": 1e3 * t_both,
+            "how": "torch copy_ between pinned host and device tensors (cudaMemcpyAsync), one stream per "
+                   "direction, best of %d" % reps}
+
+
+def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_steps, accuracy, all_cores,
+                 harvest_steps=24, train_from=None, no_mlp=False, dist=None, world=1, gpu_index=0,
+                 transfer_from=None, transfer_samples=0):
+    """One 2D3V workload: the FP32+MLP form timed over `steps` steps (CUDA
+    events per phase, clocks sampled), its roofline, the same steps with
+    cold-started fits, optionally the warm-start network trained on another
+    velocity grid (transfer_from), the end-to-end leg with the host link's
+    own copy rates, the plain FP64 form, and (rank 0) the accuracy against
+    the FP64 oracle with the oracle's rates as CPU baseline."""
+    import numpy as np
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300.driver import Simulation
+    from paper_2109_06743_gb300.warmstart import train_warm_start
+    rank = dist.get_rank() if dist else 0
+    train_from = train_from or TRAIN_FROM[name]
+    mlp_w, mlp_info = (None, None) if no_mlp else train_warm_start(train_from, device, harvest_steps=harvest_steps)
+    use_mlp = mlp_w is not None
+    cfg = make_cfg(name, precision=32)
+    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device)
+    if use_mlp:
+        abi.mlp_set_weights(sim.ctx, mlp_w)
+    stream = sim.stream
+    cells = cfg.phase_cells()
+    nsp = len(cfg.species)
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(warmup):
+        sim.step(use_mlp=use_mlp)
+    abi.vl_reset_stats(sim.ctx, stream)
+    barrier_sync()
+
+    # ---- timed region: K steps, CUDA events on the solver's stream ----------
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    elapsed, phase_ms, count, launches = timed_steps(sim, steps, use_mlp)
+    barrier_sync()
+    clk = clocks.stop()
+    stats = abi.vl_read_stats(sim.ctx, stream)
+    if stats[8]:
+        raise RuntimeError("%d tile copies of the fused sweep ran out of time: the timed steps are invalid" % stats[8])
+    abi.vl_sync_status(sim.ctx, stream)
+    elapsed = slowest(elapsed, dist, device)
+    value = job_rate(cells, steps, world, elapsed)
+
+    # ---- roofline of the dominant kernel --------------------------------------
+    peak, peak_kind = peaks()
+    per_launch_cells = cells // nsp  # one species per launch
+    rows = hbm_rows(phase_ms, count, per_launch_cells)
+    dom = max(phase_ms, key=lambda k: phase_ms[k])
+    newton = newton_roofline(cfg, stats, phase_ms.get("fit_solve"), count.get("fit_solve", 1), alu)
+    if dom in rows:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["GBps"], "peak": peak, "unit": "GB/s",
+                "frac": rows[dom]["GBps"] / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": 8 * per_launch_cells}
+    else:
+        roof = newton
+    nfit = 2 * cfg.ncell * nsp
+
+    # ---- the same steps with the cold-started fit (no network) ----------------
+    cold = None
+    if use_mlp and cold_steps > 0:
+        abi.vl_reset_stats(sim.ctx, stream)
+        barrier_sync()
+        tc_, ph_c, cnt_c, _ = timed_steps(sim, cold_steps, False)
+        cst = abi.vl_read_stats(sim.ctx, stream)
+        cold = {"value": cells * cold_steps / tc_, "unit": UNIT, "ms_per_step": 1e3 * tc_ / cold_steps,
+                "steps": cold_steps, "fit_solve_ms_per_step": ph_c.get("fit_solve", 0.0) / cold_steps,
+                "newton_iterations_per_fit": cst[0] / (nfit * cold_steps),
+                "newton_fallbacks_per_fit": cst[1] / (nfit * cold_steps)}
+
+    # ---- the network trained on another velocity grid (transfer) ---------------
+    transfer = None
+    if use_mlp and transfer_from:
+        tw, tinfo = train_warm_start(transfer_from, device, harvest_steps=max(1, transfer_samples // (
+            4 * make_cfg(transfer_from).ncell)))
+        abi.mlp_set_weights(sim.ctx, tw)
+        abi.vl_reset_stats(sim.ctx, stream)
+        barrier_sync()
+        kt = max(1, cold_steps)
+        tt, ph_t, _, _ = timed_steps(sim, kt, True)
+        tst = abi.vl_read_stats(sim.ctx, stream)
+        abi.mlp_set_weights(sim.ctx, mlp_w)
+        tinfo.update({"applied_to": "%s (%d^3 velocity cells per species)" % (name, cfg.species[0].nv[0]),
+                      "steps": kt, "ms_per_step": 1e3 * tt / kt,
+                      "fit_solve_ms_per_step": ph_t.get("fit_solve", 0.0) / kt,
+                      "newton_iterations_per_fit": tst[0] / (nfit * kt),
+                      "newton_fallbacks_per_fit": tst[1] / (nfit * kt),
+                      "fits_started_warm": tst[12] / (nfit * kt)})
+        transfer = tinfo
+
+    # ---- end to end through the public API with host buffers ------------------
+    e2e = None
+    if e2e_steps > 0:
+        host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
+        for h, f in zip(host, sim.f):
+            h.copy_(f)
+        barrier_sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.host_streams_after(e0)
+        with torch.cuda.stream(stream):
+            for _ in range(e2e_steps):
+                sim.step_through_host(host, use_mlp=use_mlp)
+            sim.wait_host()
+        e1.record(stream)
+        barrier_sync()
+        et = slowest(e0.elapsed_time(e1) / 1e3, dist, device)
+        nbytes = sum(f.numel() * f.element_size() for f in sim.f)
+        link = host_link(host, sim.f_spare or sim.f)
+        e2e = {"value": job_rate(cells, e2e_steps, world, et), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_per_step": 1e3 * et / e2e_steps,
+               "host_link": link,
+               "copy_bound_value": cells / (link["step_copy_ms_at_roof"] / 1e3)}
+        del host
+
+    fit_iters = stats[0] / max(1, nfit * steps)
+    if use_mlp:
+        mlp_info.update({"newton_iterations_per_fit": fit_iters, "newton_fallbacks_per_fit": stats[1] / (nfit * steps),
+                         "fits_started_warm": stats[12] / (nfit * steps), "cold_start": cold,
+                         "applied_to": name + " (%d^3 velocity cells per species)" % cfg.species[0].nv[0]})
+        if transfer:
+            mlp_info["transfer"] = transfer
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP64 GPU form of the same workload -------------------------
+    fp64 = None
+    if fp64_steps > 0:
+        cfg64 = make_cfg(name, precision=64)
+        s64 = Simulation(cfg64, initial_state(cfg64, np.float64), None, initial_yee(cfg64), device=device)
+        for _ in range(2):
+            s64.step()
+        abi.vl_reset_stats(s64.ctx, s64.stream)
+        torch.cuda.synchronize()
+        t64, ph64, cnt64, _ = timed_steps(s64, fp64_steps, False)
+        st64 = abi.vl_read_stats(s64.ctx, s64.stream)
+        nf64 = 2 * cfg64.ncell * len(cfg64.species) * fp64_steps
+        fp64 = {"value": cells * fp64_steps / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / fp64_steps,
+                "steps": fp64_steps, "phases_ms_per_step": {k: v / fp64_steps for k, v in sorted(ph64.items())},
+                "hbm_phases": hbm_rows(ph64, cnt64, per_launch_cells, 16),
+                "newton_iterations_per_fit": st64[0] / nf64, "newton_fallbacks_per_fit": st64[1] / nf64,
+                "fit_roofline": newton_roofline(cfg64, st64, ph64.get("fit_solve"), cnt64.get("fit_solve", 1), alu,
+                                                fp64=True),
+                "note": "same workload, FP64 f, sweeps, fluid and plain FP64 Newton fit, cold-started"}
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
+
+    acc, cb = (None, None)
+    if rank == 0 and accuracy:
+        acc, cb = subdomain_accuracy(name, mlp_w, device)
+        if all_cores:
+            cb["all_cores"] = cpu_all_cores(name)
+    return {
+        "value": value, "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * elapsed / steps,
+        "config": {"workload": name, "grid": [cfg.nx, cfg.ny], "nv": cfg.species[0].nv[0], "species": nsp,
+                   "phase_cells_per_gpu": cells,
+                   "precision": "f32 f, sweeps and fluid right-hand side; f64 moment sums, fluid state, fields; "
+                                "double-float Newton fit" + ("; BF16 warm-start network" if use_mlp else ""),
+                   "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
+                       sum(cfg.ncell * s_.vblock for s_ in cfg.species) * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof, "newton_roofline": newton,
+        "phases_ms_per_step": {k: v / steps for k, v in sorted(phase_ms.items())},
+        "hbm_phases": rows,
+        "newton_iterations_per_fit": fit_iters, "newton_fallbacks": stats[1], "clipped_cells": stats[2],
+        "mlp": mlp_info, "accuracy_vs_fp64_oracle": acc,
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64}
+
+
+def shear_ablation(device, steps=100):
+    """The velocity splitting read two ways (Sec. 2.1's backsubstitution):
+    the exact five-shear factorisation of the Boris map against the plain
+    three-shear split, on the Harris subdomain of the accuracy check (64 x 32
+    x 16^3, the workload's dx, dv and dt), FP64, fitted, `steps` steps on the
+    GPU: total-energy drift of each, and the difference of the two runs'
+    moments and reconnected flux; each form is also checked against the FP64
+    oracle with the same splitting over 2 steps on the central 16 x 8
+    subdomain."""
+    import numpy as np
+
+    import oracle
+    from oracle.step import OracleState
+    from paper_2109_06743_gb300.driver import Simulation
+    oracle.build()
+    out = {"run": "harris 64x32 x 16^3 subdomain (dx, dv, dt of harris_512x256_v16), FP64, fitted, %d steps" % steps}
+    mom = {}
+    for ns in (5, 3):
+        cfg = make_cfg("harris_512x256_v16", precision=64, sub=(64, 32))
+        cfg.nshear = ns
+        sim = Simulation(cfg, initial_state(cfg, np.float64), None, initial_yee(cfg), device=device)
+        e0, psi0 = sim.total_energy(), sim.reconnected_flux(0.0)
+        for _ in range(steps):
+            sim.step()
+        mom[ns] = [m.cpu().numpy() for m in sim.mom_t]
+        out["shears_%d" % ns] = {"energy_drift": (sim.total_energy() - e0) / e0,
+                                 "reconnected_flux_change": sim.reconnected_flux(0.0) - psi0}
+        sim.close()
+        # parity of this splitting with the oracle's
+        cs = make_cfg("harris_512x256_v16", precision=64, sub=(16, 8))
+        cs.nshear = ns
+        f0 = initial_state(cs, np.float64)
+        g = Simulation(cs, f0, None, initial_yee(cs), device=device)
+        o = OracleState(cs, f0, None, initial_yee(cs))
+        for _ in range(2):
+            g.step()
+            o.step(cs.dt)
+        out["shears_%d" % ns]["f_max_rel_diff_vs_oracle_16x8_2_steps"] = max(
+            float(np.abs(g.f_host(k) - o.f[k]).max() / o.f[k].max()) for k in range(2))
+        g.close()
+    # moments of the two runs: largest difference relative to the moment's
+    # largest magnitude over the grid
+    diffs = []
+    for a, b in zip(mom[5], mom[3]):
+        sc = np.abs(a).max(axis=0) + 1e-300
+        diffs.append(float((np.abs(a - b) / sc).max()))
+    out["moments_max_rel_diff_3_vs_5"] = max(diffs)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,12 +862,15 @@ def main():
     ap.add_argument("--workload", default="harris_512x256_v16", choices=sorted(WORKLOADS) + [LANDAU])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form timed for comparison")
+    ap.add_argument("--fp64-steps", type=int, default=10, help="steps of the FP64 form timed for comparison")
     ap.add_argument("--no-mlp", action="store_true", help="cold-started fits only (no warm-start network)")
     ap.add_argument("--train-from", default=None, choices=sorted(WORKLOADS),
                     help="workload whose fits train the warm-start network (default: the same velocity grid)")
     ap.add_argument("--harvest-steps", type=int, default=24, help="cold-started steps harvested for training")
     ap.add_argument("--no-all-cores", action="store_true", help="skip the all-cores oracle figure")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="only the named workload: no nested lines of the other workloads, no network transfer, "
+                         "no shear ablation")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -521,13 +881,10 @@ def main():
     if args.workload == LANDAU:
         return run_landau(args, rank)
 
-    import numpy as np
     import torch
 
     from paper_2109_06743_gb300 import abi
     from paper_2109_06743_gb300 import build as B
-    from paper_2109_06743_gb300.driver import Simulation
-    from paper_2109_06743_gb300.warmstart import train_warm_start
 
     torch.cuda.set_device(local)
     dist = None
@@ -542,180 +899,33 @@ def main():
 
     device = "cuda:%d" % local
     affinity = pin_host_to_gpu(local)
-    train_from = args.train_from or TRAIN_FROM[args.workload]
-    mlp_w, mlp_info = (None, None) if args.no_mlp else train_warm_start(train_from, device,
-                                                                         harvest_steps=args.harvest_steps)
-    use_mlp = mlp_w is not None
-    cfg = make_cfg(args.workload, precision=32)
-    f0 = initial_state(cfg, np.float32)
-    sim = Simulation(cfg, f0, None, initial_yee(cfg), device=device)
-    if use_mlp:
-        abi.mlp_set_weights(sim.ctx, mlp_w)
-    stream = sim.stream
-    cells = cfg.phase_cells()
-
-    def barrier_sync():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        sim.step(use_mlp=use_mlp)
-    abi.vl_reset_stats(sim.ctx, stream)
-    barrier_sync()
-
-    # ---- timed region: K steps, CUDA events on the solver's stream ----------
-    phase_ms = {}
-    pending = []
-    cur = {"label": None, "ev": None}
-
-    def mark(label):
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        if cur["label"] is not None:
-            pending.append((cur["label"], cur["ev"], ev))
-        cur["label"], cur["ev"] = label, ev
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = abi.vl_launch_count()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        sim.step(use_mlp=use_mlp, mark=mark)
-    t_end.record(stream)
-    barrier_sync()
-    launches = abi.vl_launch_count() - launches0
-    clk = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
-    count = {}
-    for label, e0, e1 in pending:
-        phase_ms[label] = phase_ms.get(label, 0.0) + e0.elapsed_time(e1)
-        count[label] = count.get(label, 0) + 1
-    stats = abi.vl_read_stats(sim.ctx, stream)
-    if stats[8]:
-        raise RuntimeError("%d tile copies of the fused sweep ran out of time: the timed steps are invalid" % stats[8])
-    elapsed = slowest(elapsed, dist, device)
-    value = job_rate(cells, args.steps, world, elapsed)
-
-    # ---- roofline of the dominant kernel --------------------------------------
-    peak, peak_kind = peaks()
-    per_launch_cells = cells // len(cfg.species)  # one species per launch
-    hbm_phases = {"xy_sweep": 8, "x_sweep": 8, "y_sweep": 8, "v_pass": 8, "fit_exchange": 8}
-    dom = max(phase_ms, key=lambda k: phase_ms[k])
-    rows = {}
-    for ph, b in hbm_phases.items():
-        if ph in phase_ms:
-            avg_s = phase_ms[ph] / count[ph] / 1e3
-            rows[ph] = {"ms_per_launch": avg_s * 1e3, "GBps": b * per_launch_cells / avg_s / 1e9,
-                        "frac_of_%s_hbm" % peak_kind: b * per_launch_cells / avg_s / 1e9 / peak}
-    newton = newton_roofline(cfg, stats, phase_ms.get("fit_solve"), count.get("fit_solve", 1))
-    if dom in hbm_phases:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["GBps"], "peak": peak, "unit": "GB/s",
-                "frac": rows[dom]["GBps"] / peak, "traffic": None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": 8 * per_launch_cells}
-    else:
-        roof = newton
-
-    # ---- the same steps with the cold-started fit (no network) ----------------
-    cold = None
-    if use_mlp:
-        kc = max(1, min(args.steps, 5))
-        abi.vl_reset_stats(sim.ctx, stream)
-        barrier_sync()
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(kc):
-            sim.step(use_mlp=False)
-        c1.record(stream)
-        barrier_sync()
-        tc_ = c0.elapsed_time(c1) / 1e3
-        cst = abi.vl_read_stats(sim.ctx, stream)
-        nfit = 2 * cfg.ncell * len(cfg.species)
-        cold = {"value": cells * kc / tc_, "unit": UNIT, "ms_per_step": 1e3 * tc_ / kc, "steps": kc,
-                "newton_iterations_per_fit": cst[0] / (nfit * kc), "newton_fallbacks_per_fit": cst[1] / (nfit * kc)}
-
-    # ---- end to end through the public API with host buffers ------------------
-    e2e = None
-    if not args.no_e2e:
-        host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
-        for h, f in zip(host, sim.f):
-            h.copy_(f)
-        barrier_sync()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ksteps = max(1, min(args.steps, 10))
-        e0.record(stream)
-        sim.host_streams_after(e0)
-        with torch.cuda.stream(stream):
-            for _ in range(ksteps):
-                sim.step_through_host(host, use_mlp=use_mlp)
-            sim.wait_host()
-        e1.record(stream)
-        barrier_sync()
-        et = slowest(e0.elapsed_time(e1) / 1e3, dist, device)
-        nbytes = sum(f.numel() * f.element_size() for f in sim.f)
-        e2e = {"value": job_rate(cells, ksteps, world, et), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": ksteps}
-
-    nfits = max(1, 2 * cfg.ncell * len(cfg.species) * args.steps)
-    fit_iters = stats[0] / nfits
-    if use_mlp:
-        mlp_info.update({"newton_iterations_per_fit": fit_iters, "newton_fallbacks_per_fit": stats[1] / nfits,
-                         "cold_start": cold,
-                         "applied_to": args.workload + " (%d^3 velocity cells per species)" % cfg.species[0].nv[0]})
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
-
-    # ---- the plain FP64 GPU form of the same workload -------------------------
-    fp64 = None
-    if args.fp64_steps > 0:
-        cfg64 = make_cfg(args.workload, precision=64)
-        s64 = Simulation(cfg64, initial_state(cfg64, np.float64), None, initial_yee(cfg64),
-                         device="cuda:%d" % local)
-        for _ in range(3):
-            s64.step()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(s64.stream)
-        for _ in range(args.fp64_steps):
-            s64.step()
-        b.record(s64.stream)
-        torch.cuda.synchronize()
-        t64 = a.elapsed_time(b) / 1e3
-        fp64 = {"value": cells * args.fp64_steps / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.fp64_steps,
-                "steps": args.fp64_steps, "note": "same workload with FP64 f and sweeps, single GPU"}
-        s64.close()
-
-    if rank != 0:
-        return 0
-    acc, cb = (None, None) if args.no_cpu else subdomain_accuracy(args.workload, mlp_w, device)
-    if cb is not None and not args.no_all_cores:
-        cb["all_cores"] = cpu_all_cores(args.workload)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [cfg.nx, cfg.ny], "nv": cfg.species[0].nv[0],
-                   "species": len(cfg.species), "phase_cells_per_gpu": cells,
-                   "precision": "f32 f, sweeps and fluid right-hand side; f64 moment sums, fluid state, fields; "
-                                "double-float Newton fit" + ("; BF16 warm-start network" if use_mlp else ""),
-                   "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
-                       sum(cfg.ncell * s.vblock for s in cfg.species) * 4 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single", "host_cores": affinity},
-        "roofline": roof,
-        "phases_ms_per_step": {k: v / args.steps for k, v in sorted(phase_ms.items())},
-        "hbm_phases": rows,
-        "newton_iterations_per_fit": fit_iters, "newton_fallbacks": stats[1], "clipped_cells": stats[2],
-        "mlp": mlp_info, "accuracy_vs_fp64_oracle": acc,
-        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64,
-    }
-    print(json.dumps(line))
+    alu = measured_alu_peaks(device)
+    extra = not args.no_extra and args.workload == "harris_512x256_v16"
+    res = measure_2d3v(args.workload, device, alu, args.steps, args.warmup, 0 if args.no_e2e else min(args.steps, 10),
+                       max(1, min(args.steps, 5)), args.fp64_steps, not args.no_cpu, not args.no_all_cores,
+                       harvest_steps=args.harvest_steps, train_from=args.train_from, no_mlp=args.no_mlp, dist=dist,
+                       world=world, gpu_index=local,
+                       transfer_from="harris_128x64_v20" if extra and not args.no_mlp else None,
+                       transfer_samples=10_000_000)
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    line.update({k: v for k, v in res.items() if k not in ("value", "steps", "warmup", "ms_per_step")})
+    line["config"]["host_cores"] = affinity
+    line["alu_peaks"] = alu
+    if extra:
+        # the other workloads of the metric, a few timed steps each (rank 0's
+        # GPU; under torchrun the other ranks time their own replicas alike)
+        nested = {}
+        nested["asym_1024x512_v12"] = measure_2d3v(
+            "asym_1024x512_v12", device, alu, 5, 2, 3, 3, 3 if args.fp64_steps else 0, not args.no_cpu, False,
+            dist=dist, world=world, gpu_index=local)
+        if rank == 0:
+            nested[LANDAU] = landau_block(200, 3)
+            line["shear_ablation"] = shear_ablation(device)
+        line["workloads"] = nested
+    if rank == 0:
+        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0

@@ -11,10 +11,20 @@
  *
  * Error behaviour: argument errors return VL_EINVAL immediately (nothing is
  * enqueued) and vl_last_error() describes them; a failed kernel launch returns
- * VL_ECUDA. Kernels that detect a problem on the device (non-finite or
- * negative input moments, Newton fallbacks) count it in device-side counters
- * read with vl_read_stats(); Newton non-convergence is not fatal: the
- * continuous Maxwellian of the targets is used and counted.
+ * VL_ECUDA. Numeric errors found on the device (fit targets, i.e. moments of
+ * f or fluid state, that are not finite or have n < 0) set the context's
+ * status word; the next compute call on the context then returns VL_ENUMERIC
+ * without enqueueing anything and clears the word, and vl_sync_status()
+ * synchronises the stream and returns it. Because the calls are asynchronous
+ * the error is returned by the first call made after the kernel that found
+ * it has run (at the latest by vl_sync_status). Empty cells (n = 0) are not
+ * an error. Newton non-convergence is not fatal: the continuous Maxwellian of
+ * the targets is used and counted (vl_read_stats()). The status word is 4
+ * bytes of pinned host memory mapped into the device, allocated by
+ * vlasov_init and freed by vlasov_free (the only allocation of the library).
+ * The library must not be used across a cudaDeviceReset of a device it has
+ * run on (contexts and pfc_advect_v_static's cached scratch address refer to
+ * that device's context).
  *
  * Layouts (row-major, fastest index last):
  *   f_s        [ny][nx][nvz][nvy][nvx] of float (precision 32) or double (64);
@@ -52,7 +62,8 @@ typedef enum {
     VL_EINVAL = 1,   /* invalid argument or descriptor                    */
     VL_ECUDA = 2,    /* a CUDA call or kernel launch failed               */
     VL_ENOCONV = 3,  /* (stats only) Newton fallback was used             */
-    VL_ENUMERIC = 4, /* (stats only) non-finite or negative input moments */
+    VL_ENUMERIC = 4, /* non-finite or negative fit targets found on the device
+                        (returned by the next call or by vl_sync_status) */
     VL_ENOTSUP = 5   /* valid but unsupported shape (e.g. non-cubic block) */
 } vl_status;
 
@@ -96,8 +107,16 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
                       double* yee_dev, double* eb_dev, void* work_dev,
                       size_t work_bytes, vl_ctx** out);
 vl_status vlasov_free(vl_ctx* ctx);
-/* Human-readable description of the last error on this context (never NULL). */
+/* Human-readable description of the last error on this context (never NULL).
+ * With ctx = NULL: the last error of a call made without a context (or that
+ * failed before creating one) on the calling host thread. */
 const char* vl_last_error(const vl_ctx* ctx);
+
+/* Waits for the stream, then returns the context's status word: VL_ENUMERIC
+ * if a kernel found non-finite or negative fit targets since the word was
+ * last reported (the word is then cleared), VL_ECUDA if the stream failed,
+ * else VL_OK. Paper Sec. 2.2 (the fit targets of Algorithm 1). */
+vl_status vl_sync_status(vl_ctx* ctx, vl_stream_t stream);
 
 /* Spatial PFC sweep of species s along axis 0 (x, periodic) or 1 (y, periodic
  * or reflecting walls with f(-y, v_y) = f(y, -v_y)), displacement v_a dt per
@@ -146,7 +165,11 @@ vl_status pfc_advect_v(vl_ctx* ctx, int species, double dt, double* mom_out,
  * operation) with that device current; make it before any stream capture.
  * Every call shares the array: nothing in it has to start at zero (each call
  * writes every row it reads), but calls that overlap in time on one device
- * race on it. Errors are reported through vl_last_error(NULL). */
+ * race on it. f_dev must be aligned to its element size, eb_dev and mom_out
+ * to 8 bytes, and mom_out must not overlap f_dev (VL_EINVAL otherwise,
+ * before any launch). The cached address is that of the device's current
+ * context: do not call across a cudaDeviceReset. Errors are reported through
+ * vl_last_error(NULL) on the calling thread. */
 #define VL_STATIC_SCRATCH_CELLS 32768
 vl_status pfc_advect_v_static(const vl_desc* desc, int species, void* f_dev,
                               const double* eb_dev, long long ncell, double dt,
@@ -158,8 +181,10 @@ vl_status moments(vl_ctx* ctx, int species, double* mom_out, vl_stream_t stream)
 /* Moment fitting of Algorithm 1 (Sec. 2.2) for species s. vmom: raw moments
  * of the current f ([ncell][20], e.g. from pfc_advect_v). The fluid moments
  * of the context are rescaled by n_V/n_F; two discrete Maxwellians are fitted
- * by FP64 Newton iteration (their midpoint moments of degree <= 2 equal the
- * V and the rescaled F targets); then f <- f - f_M,V + f_M,F, negative values
+ * by Newton iteration (their midpoint moments of degree <= 2 equal the
+ * V and the rescaled F targets; precision 64: plain FP64 arithmetic;
+ * precision 32: double-float arithmetic, about 44 significant bits, on the
+ * FP32 pipe, with an FP32 Jacobian); then f <- f - f_M,V + f_M,F, negative values
  * are clipped and the cell rescaled to n_V (limiter of Algorithm 1). The
  * fluid state is replaced by its rescaled moments. use_mlp != 0 starts Newton
  * from the network's prediction (see the MLP section below; needs weights
@@ -182,17 +207,23 @@ vl_status moment_fit_solve(vl_ctx* ctx, int species, const double* vmom, int use
 vl_status moment_fit_exchange(vl_ctx* ctx, int species, const double* vmom,
                               double* mom_out, vl_stream_t stream);
 
-/* Selects how the 2D3V Newton fits of this species (Sec. 2.2, Algorithm 1's
- * moment fitting) evaluate a discrete Maxwellian whose values span more than
- * the float range over the velocity block, i.e. one that is narrow against
- * a velocity box sized for a hotter population (values falling below e^-80
- * of the peak towards the box's corners). wide = 0 (the default): one FP64
- * exponential per velocity cell for such blocks, and the fit kernel holds
- * only the common evaluation. wide = 1: a fit kernel that also holds the
- * centre-out double-float recurrences, which evaluate such blocks at the
- * common evaluation's speed. The fitted Maxwellians agree to rounding either
- * way. Takes effect from the next moment_fit(_solve) of the species; host
- * only, no launch. VL_EINVAL for a bad species. */
+/* Selects how the double-float 2D3V Newton fits of this species (precision
+ * 32; Sec. 2.2, Algorithm 1's moment fitting) evaluate a discrete Maxwellian
+ * whose values span more than the float range over the velocity block, i.e.
+ * one that is narrow against a velocity box sized for a hotter population
+ * (values falling below e^-80 of the peak towards the box's corners).
+ * wide < 0 (the default): chosen on the device at every fit from the targets,
+ * without a host synchronisation: the wide kernel if some cell with at least
+ * 1e-10 of the largest density has a V or F Maxwellian that falls by more
+ * than 60 e-folds from its peak to the farthest corner of the box, else the
+ * common one (both kernels are launched; the one not chosen returns at
+ * once). wide = 0: always the common kernel (one FP64 exponential per
+ * velocity cell for such blocks). wide = 1: always the kernel that also
+ * holds the centre-out double-float recurrences, which evaluate such blocks
+ * at the common evaluation's speed. The fitted Maxwellians agree to rounding
+ * either way; vl_read_stats counts the fits of the wide kernel. Takes effect
+ * from the next moment_fit(_solve) of the species; host only, no launch.
+ * VL_EINVAL for a bad species. */
 vl_status moment_fit_wide(vl_ctx* ctx, int species, int wide);
 
 /* One SSP-RK3 step (Shu-Osher 1988) of the ten-moment equations of Sec. 2.1
@@ -275,22 +306,36 @@ vl_status mlp_grad(vl_ctx* ctx, const float* samples_dev, long long n, float* gr
                    double* loss_host, vl_stream_t stream);
 
 /* Device counters accumulated since the last reset: out[0] Newton
- * iterations, out[1] Newton fallbacks, out[2] clipped cells, out[3] cells
- * with non-finite or non-positive targets; the work of the 2D3V Newton fits
- * (each counted once per fit and evaluation, over the whole velocity block):
- * out[4] double-float moment evaluations (recurrence path), out[5] FP32
- * Jacobian (Gram) evaluations, out[6] evaluations with one FP64 exponential
- * per velocity cell (wide exponent range), out[7] Newton steps with the
- * FP64 Jacobian; out[8] asynchronous tile copies whose wait ran out of time
- * (the fused spatial sweep gives up on such a tile and leaves it unwritten:
- * any nonzero value means the result of that call is invalid). Synchronises
- * the stream. */
-#define VL_NSTATS 9
+ * iterations, out[1] Newton fallbacks, out[2] clipped cells, out[3] fits
+ * whose targets are invalid (empty, non-finite or not positive definite);
+ * the work of the double-float 2D3V Newton fits (precision 32; each counted
+ * once per fit and evaluation, over the whole velocity block): out[4]
+ * double-float moment evaluations (recurrence path), out[5] FP32 Jacobian
+ * (Gram) evaluations, out[6] evaluations with one FP64 exponential per
+ * velocity cell (wide exponent range), out[7] Newton steps with the FP64
+ * Jacobian; out[8] asynchronous tile copies whose wait ran out of time (the
+ * fused spatial sweep gives up on such a tile and leaves it unwritten: any
+ * nonzero value means the result of that call is invalid); out[9] fits run
+ * by the wide double-float kernel; the work of the FP64 fits (precision 64):
+ * out[10] moment evaluations, out[11] of which with the Gram sums; out[12]
+ * fits started from the network's prediction (use_mlp, prediction accepted
+ * by the network's input and output range guard). Synchronises the stream. */
+#define VL_NSTATS 13
 vl_status vl_read_stats(vl_ctx* ctx, long long out[VL_NSTATS], vl_stream_t stream);
 vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream);
 
 /* Number of kernels this library has launched (all contexts, process-wide). */
 long long vl_launch_count(void);
+
+/* Measured fused multiply-add throughput of the current device in FP32
+ * (precision 32) or FP64 (64), in operations per second (a fused
+ * multiply-add counted as one operation): a kernel of independent FMA
+ * chains, eight 256-thread blocks per SM, timed with CUDA events on the
+ * stream after one untimed launch; it changes no device setting. The
+ * denominator of the Newton fits' ALU roofline; the paper has no
+ * counterpart. sink_dev: 8 bytes of device memory (8-byte aligned) that the
+ * kernel could write but never does. Synchronises the stream. */
+vl_status vl_fma_peak(int precision, double* ops_per_s, void* sink_dev, vl_stream_t stream);
 
 #ifdef __cplusplus
 }

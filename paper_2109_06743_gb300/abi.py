@@ -13,13 +13,13 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvlasov.so")
 MAX_SPECIES = 4
-NSTATS = 9  # VL_NSTATS
+NSTATS = 13  # VL_NSTATS
 
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
             "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "moment_fit_wide", "fluid_step",
-            "fluid_step_closure", "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_launch_count", "mlp_init", "mlp_set_weights",
+            "fluid_step_closure", "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_sync_status", "vl_launch_count", "vl_fma_peak", "mlp_init", "mlp_set_weights",
             "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
             "mlp_grad"]
 MLP_NPARAM = 19520  # VL_MLP_NPARAM
@@ -91,6 +91,8 @@ def lib():
     L.fluid_step_closure.argtypes = [_vp, ctypes.c_double, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.vl_reset_stats.argtypes = [_vp, _vp]
+    L.vl_sync_status.argtypes = [_vp, _vp]
+    L.vl_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp, _vp]
     F = ctypes.POINTER(ctypes.c_float)
     L.mlp_init.argtypes = [_vp, ctypes.c_ulonglong]
     L.mlp_set_weights.argtypes = [_vp, F]
@@ -223,7 +225,8 @@ def moment_fit_exchange(ctx, species, vmom, mom_out=None, stream=None):
 
 
 def moment_fit_wide(ctx, species, wide):
-    _check(ctx, lib().moment_fit_wide(ctx, species, int(bool(wide))))
+    """wide: None (chosen on the device), False/0 or True/1."""
+    _check(ctx, lib().moment_fit_wide(ctx, species, -1 if wide is None else int(bool(wide))))
 
 
 def fluid_step(ctx, dt, mom_t, mom_t1, stream=None):
@@ -305,3 +308,17 @@ def mlp_grad(ctx, samples, n, grad, stream=None):
     loss = ctypes.c_double(0.0)
     _check(ctx, lib().mlp_grad(ctx, ptr(samples), int(n), ptr(grad), ctypes.byref(loss), stream_handle(stream)))
     return loss.value
+
+
+def vl_sync_status(ctx, stream=None):
+    """Wait for the stream; raises VlasovError(VL_ENUMERIC) if a kernel found
+    non-finite or negative fit targets since the status was last reported."""
+    _check(ctx, lib().vl_sync_status(ctx, stream_handle(stream)))
+
+
+def vl_fma_peak(precision, sink, stream=None):
+    """Measured FMA operations per second of the current device (FP32 or
+    FP64); sink: an 8-byte device tensor the probe never writes."""
+    out = ctypes.c_double(0.0)
+    _check(None, lib().vl_fma_peak(int(precision), ctypes.byref(out), ptr(sink), stream_handle(stream)))
+    return out.value

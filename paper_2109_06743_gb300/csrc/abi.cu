@@ -34,7 +34,9 @@ struct vl_ctx {
     int adam_step;
     float* harvest;
     long long harvest_cap;
-    bool fit_wide[VL_MAX_SPECIES];  // moment_fit_wide
+    int fit_mode[VL_MAX_SPECIES];   // moment_fit_wide: -1 chosen on the device, 0 common, 1 wide
+    int* status_host;               // status word: pinned host memory mapped into the device
+    int* status_dev;                // its device-side address
     char err[512];
 };
 
@@ -48,7 +50,8 @@ void count_launch(int n) { g_launches.fetch_add(n); }
 
 namespace {
 
-char g_err[512] = "";
+// errors of calls without a context (per host thread)
+thread_local char g_err[512] = "";
 
 vl_status fail(vl_ctx* ctx, vl_status st, const char* fmt, ...) {
     char* buf = ctx ? ctx->err : g_err;
@@ -73,7 +76,7 @@ long long vblock_of(const vl_desc& d, int s) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, fluid_f, counters;
+    size_t cellwork, coef_v, coef_f, status, u1, u2, cur, fluid_f, counters, select;
     size_t mlp_w, mlp_m, mlp_v, mlp_g, mlp_acc, mlp_err, mlp_pred, harvest_count, total;
 };
 
@@ -90,6 +93,7 @@ Layout layout_of(const vl_desc& d) {
     L.cur = off; off = align256(off + nc * 3 * sizeof(double));
     L.fluid_f = off; off = align256(off + 2 * nc * 10 * sizeof(float));
     L.counters = off; off = align256(off + VL_NSTATS * sizeof(unsigned long long));
+    L.select = off; off = align256(off + 2 * sizeof(unsigned long long));
     const size_t np = (size_t)VL_MLP_NPARAM * sizeof(float);
     L.mlp_w = off; off = align256(off + np);
     L.mlp_m = off; off = align256(off + np);
@@ -157,8 +161,27 @@ void fill_box(const vl_desc& d, int s, double* vmin, double* dv) {
     }
 }
 
+// The status word: a kernel that finds a numeric error (non-finite or
+// negative fit targets) writes VL_ENUMERIC there; the next compute call on
+// the context reports it (and clears it) instead of enqueueing its work.
+vl_status pending_numeric(vl_ctx* ctx) {
+    volatile int* w = ctx->status_host;
+    const int v = *w;
+    if (v == VL_OK) return VL_OK;
+    *w = VL_OK;
+    return fail(ctx, (vl_status)v,
+                "a kernel of an earlier call found non-finite or negative fit targets (moments of f or fluid state)");
+}
+
+vl_status check_ctx(vl_ctx* ctx) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    return pending_numeric(ctx);
+}
+
 vl_status check_species(vl_ctx* ctx, int s) {
     if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    vl_status st = pending_numeric(ctx);
+    if (st != VL_OK) return st;
     if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species %d out of range", s);
     if (!ctx->f[s]) return fail(ctx, VL_EINVAL, "species %d has no distribution function (fluid-only context)", s);
     return VL_OK;
@@ -187,8 +210,19 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     if (!work_dev || work_bytes < L.total)
         return fail(nullptr, VL_EINVAL, "workspace too small: %zu bytes given, %zu needed", work_bytes, L.total);
     if (((uintptr_t)work_dev & 255u) != 0) return fail(nullptr, VL_EINVAL, "workspace must be 256-byte aligned");
+    int* word = nullptr;
+    int* word_dev = nullptr;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&word), sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *word = VL_OK;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&word_dev), word, 0);
+        if (e != cudaSuccess) cudaFreeHost(word);
+    }
+    if (e != cudaSuccess) return fail(nullptr, VL_ECUDA, "status word: %s", cudaGetErrorString(e));
     vl_ctx* c = new vl_ctx();
     c->d = *desc;
+    c->status_host = word;
+    c->status_dev = word_dev;
     for (int s = 0; s < VL_MAX_SPECIES; ++s) c->f[s] = (f_dev && s < desc->nspecies) ? f_dev[s] : nullptr;
     c->fluid = fluid_dev;
     c->yee = yee_dev;
@@ -204,6 +238,7 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
     c->ws.cur = reinterpret_cast<double*>(w + L.cur);
     c->ws.fluid_f = reinterpret_cast<float*>(w + L.fluid_f);
     c->ws.counters = reinterpret_cast<unsigned long long*>(w + L.counters);
+    c->ws.fit_select = reinterpret_cast<unsigned long long*>(w + L.select);
     c->ws.mlp = nullptr;
     c->mlp_w = reinterpret_cast<float*>(w + L.mlp_w);
     c->mlp_m = reinterpret_cast<float*>(w + L.mlp_m);
@@ -223,9 +258,11 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
         fill_box(*desc, s, vmin, dv);
         vl::make_mom_conv(vmin, dv, desc->nv[s][0], &c->conv[s]);
     }
+    for (int s = 0; s < VL_MAX_SPECIES; ++s) c->fit_mode[s] = -1;
     c->err[0] = 0;
-    cudaError_t e = cudaMemset(c->ws.counters, 0, VL_NSTATS * sizeof(unsigned long long));
+    e = cudaMemset(c->ws.counters, 0, VL_NSTATS * sizeof(unsigned long long));
     if (e != cudaSuccess) {
+        cudaFreeHost(c->status_host);
         delete c;
         return fail(nullptr, VL_ECUDA, "clearing counters: %s", cudaGetErrorString(e));
     }
@@ -234,8 +271,16 @@ vl_status vlasov_init(const vl_desc* desc, void* const* f_dev, double* fluid_dev
 }
 
 vl_status vlasov_free(vl_ctx* ctx) {
+    if (ctx && ctx->status_host) cudaFreeHost(ctx->status_host);
     delete ctx;
     return VL_OK;
+}
+
+vl_status vl_sync_status(vl_ctx* ctx, vl_stream_t stream) {
+    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    vl_status st = cuda_check(ctx, cudaStreamSynchronize((cudaStream_t)stream), "vl_sync_status");
+    if (st != VL_OK) return st;
+    return pending_numeric(ctx);
 }
 
 const char* vl_last_error(const vl_ctx* ctx) { return ctx ? ctx->err : g_err; }
@@ -424,6 +469,21 @@ vl_status pfc_advect_v_static(const vl_desc* desc, int s, void* f_dev, const dou
     if (ncell == 0) return VL_OK;
     if (!f_dev || !eb_dev) return fail(nullptr, VL_EINVAL, "f_dev and eb_dev are required");
     if (!std::isfinite(dt)) return fail(nullptr, VL_EINVAL, "dt is not finite");
+    {
+        // misaligned pointers would fault in the kernels' element and FP64
+        // accesses; overlapping outputs would corrupt f
+        const size_t es = d.precision == 64 ? 8 : 4;
+        const uintptr_t fp = reinterpret_cast<uintptr_t>(f_dev);
+        if (fp % es != 0) return fail(nullptr, VL_EINVAL, "f_dev is not aligned to its element size (%zu bytes)", es);
+        if (reinterpret_cast<uintptr_t>(eb_dev) % 8 != 0) return fail(nullptr, VL_EINVAL, "eb_dev is not 8-byte aligned");
+        if (mom_out) {
+            const uintptr_t mp = reinterpret_cast<uintptr_t>(mom_out);
+            if (mp % 8 != 0) return fail(nullptr, VL_EINVAL, "mom_out is not 8-byte aligned");
+            const uintptr_t fbytes = (uintptr_t)ncell * (uintptr_t)vblock_of(d, s) * es;
+            const uintptr_t mbytes = (uintptr_t)ncell * (d.nvdim == 1 ? 4 : 20) * sizeof(double);
+            if (mp < fp + fbytes && fp < mp + mbytes) return fail(nullptr, VL_EINVAL, "mom_out overlaps f_dev");
+        }
+    }
     void* scratch = nullptr;
     st = cuda_check(nullptr, vl::static_scratch_address(&scratch), "pfc_advect_v_static (scratch address)");
     if (st != VL_OK) return st;
@@ -461,7 +521,7 @@ vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
 vl_status moment_fit_wide(vl_ctx* ctx, int s, int wide) {
     if (!ctx) return VL_EINVAL;
     if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species out of range");
-    ctx->fit_wide[s] = wide != 0;
+    ctx->fit_mode[s] = wide < 0 ? -1 : (wide != 0 ? 1 : 0);
     return VL_OK;
 }
 
@@ -491,8 +551,20 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
     for (int q = 0; q < 3; ++q) a.vmax[q] = a.vmin[q] + a.dv[q] * (d.nvdim == 3 || q == 0 ? d.nv[s][q] : 1);
     a.tol = d.fit_tol;
     a.max_iter = d.fit_max_iter;
-    a.wide = ctx->fit_wide[s] ? 1 : 0;
+    a.fp64 = d.precision == 64 ? 1 : 0;
+    a.numeric = ctx->status_dev;
+    a.wide = a.fp64 ? 0 : ctx->fit_mode[s];
+    a.select = nullptr;
     cudaStream_t cs = (cudaStream_t)stream;
+    if (d.nvdim == 3 && a.wide < 0) {
+        // the double-float kernel is chosen on the device from the targets
+        st = cuda_check(ctx, cudaMemsetAsync(ctx->ws.fit_select, 0, 2 * sizeof(unsigned long long), cs),
+                        "moment_fit (kernel choice)");
+        if (st != VL_OK) return st;
+        st = cuda_check(ctx, vl::launch_fit_select(a, ctx->ws.fit_select, cs), "moment_fit (kernel choice)");
+        if (st != VL_OK) return st;
+        a.select = ctx->ws.fit_select;
+    }
     if (use_mlp) {
         vl::MlpInferArgs m;
         m.w = ctx->mlp_w;
@@ -553,7 +625,10 @@ vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double
 }
 
 vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
-    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    {
+        const vl_status st0 = check_ctx(ctx);
+        if (st0 != VL_OK) return st0;
+    }
     const vl_desc& d = ctx->d;
     if (d.nvdim != 3) return fail(ctx, VL_EINVAL, "the gradient-closure fluid model is 2D3V");
     if (!std::isfinite(dt)) return fail(ctx, VL_EINVAL, "dt is not finite");
@@ -599,7 +674,10 @@ vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
 
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,
                      vl_stream_t stream) {
-    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    {
+        const vl_status st0 = check_ctx(ctx);
+        if (st0 != VL_OK) return st0;
+    }
     if (!mom_t || !mom_t1) return fail(ctx, VL_EINVAL, "moment arrays are NULL");
     const vl_desc& d = ctx->d;
     const int ncomp = d.nvdim == 1 ? 3 : 10;
@@ -644,7 +722,10 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
 }
 
 vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_stream_t stream) {
-    if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
+    {
+        const vl_status st0 = check_ctx(ctx);
+        if (st0 != VL_OK) return st0;
+    }
     const vl_desc& d = ctx->d;
     const int ncomp = d.nvdim == 1 ? 3 : 10;
     const int nmom = d.nvdim == 1 ? 4 : 20;
@@ -877,5 +958,13 @@ vl_status vl_reset_stats(vl_ctx* ctx, vl_stream_t stream) {
 }
 
 long long vl_launch_count(void) { return vl::g_launches.load(); }
+
+vl_status vl_fma_peak(int precision, double* ops_per_s, void* sink_dev, vl_stream_t stream) {
+    if (precision != 32 && precision != 64) return fail(nullptr, VL_EINVAL, "precision must be 32 or 64");
+    if (!ops_per_s || !sink_dev) return fail(nullptr, VL_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(sink_dev) % 8 != 0) return fail(nullptr, VL_EINVAL, "sink_dev is not 8-byte aligned");
+    *ops_per_s = 0.0;
+    return cuda_check(nullptr, vl::fma_peak(precision, ops_per_s, sink_dev, (cudaStream_t)stream), "vl_fma_peak");
+}
 
 }  // extern "C"

@@ -42,12 +42,14 @@ struct Workspace {
     double* cur;          // [ncell][3] current density at cell centres
     float* fluid_f;       // [2][ncell][10] FP32 copies of a stage's state and third moments
     unsigned long long* counters;  // [VL_NSTATS]
+    unsigned long long* fit_select;  // [2] device-side choice of the fit kernel (fit_select_kernel)
     float* mlp;           // MLP weights and scratch
 };
 
 // indices of the device counters (vl_read_stats)
 enum { CNT_ITERS = 0, CNT_FALLBACK = 1, CNT_CLIPPED = 2, CNT_INVALID = 3, CNT_EVAL_M = 4, CNT_EVAL_G = 5,
-       CNT_EVAL_SLOW = 6, CNT_PRECISE = 7, CNT_COPY_TIMEOUT = 8 };
+       CNT_EVAL_SLOW = 6, CNT_PRECISE = 7, CNT_COPY_TIMEOUT = 8, CNT_WIDE_FITS = 9, CNT_EVAL64_M = 10,
+       CNT_EVAL64_G = 11, CNT_WARM = 12 };
 
 __host__ __device__ inline int ifloor(double x) { return (int)floor(x); }
 

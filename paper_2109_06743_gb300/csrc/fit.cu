@@ -420,6 +420,13 @@ __global__ void fit1d_kernel(FitArgs a) {
     const bool lead = (threadIdx.x & 31) == 0;
     double tv[3] = {a.vmom[c * 4], a.vmom[c * 4 + 1], a.vmom[c * 4 + 2]};
     const double nF = a.fluid[c * 3];
+    // non-finite or negative targets: a numeric error upstream (empty cells,
+    // n = 0, are not)
+    if (lead && a.numeric) {
+        bool bad = !(tv[0] >= 0.0) || !(nF >= 0.0);
+        for (int q = 0; q < 3; ++q) bad = bad || !isfinite(tv[q]) || !isfinite(a.fluid[c * 3 + q]);
+        if (bad) *reinterpret_cast<volatile int*>(a.numeric) = VL_ENUMERIC;
+    }
     const double scale = nF > 0.0 ? tv[0] / nF : 0.0;
     double tf[3];
     for (int q = 0; q < 3; ++q) tf[q] = a.fluid[c * 3 + q] * scale;

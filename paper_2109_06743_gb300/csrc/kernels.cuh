@@ -123,9 +123,20 @@ struct FitArgs {
     double vmin[3], dv[3], vmax[3];
     double tol;
     int max_iter;
-    int wide;               // 1: the fit kernel with the centre-out evaluation (moment_fit_wide)
+    int wide;               // 1: the fit kernel with the centre-out evaluation, 0: the common
+                            // one, -1: chosen on the device from select (moment_fit_wide)
+    const unsigned long long* select;  // wide = -1: [2] FP64 bits of the largest n over all
+                            // cells and over the cells that need the wide kernel (fit_select)
+    int fp64;               // 1: the plain FP64 fit (FP64 mode), 0: double-float on the FP32 pipe
+    int* numeric;           // status word (device-visible host memory): set to VL_ENUMERIC when
+                            // a target is not finite or has n < 0; may be null
 };
 cudaError_t launch_fit(const FitArgs& a, int nvdim, cudaStream_t st);
+// auto choice of the 2D3V fit kernel: sel[0], sel[1] (zeroed by the caller) get
+// the FP64 bits of the largest n over all cells and over the cells whose V or
+// F Maxwellian falls by more than 60 e-folds from its peak to the farthest
+// corner of the velocity box
+cudaError_t launch_fit_select(const FitArgs& a, unsigned long long* sel, cudaStream_t st);
 
 // ---- MLP warm start (mlp.cu) ------------------------------------------------------
 struct MlpInferArgs {
@@ -210,5 +221,8 @@ cudaError_t launch_current(double* cur, const double* const* src, const double* 
                            int stride, int off, long long ncell, int nvdim, double bg, cudaStream_t st);
 cudaError_t launch_maxwell(const FieldArgs& a, cudaStream_t st);
 cudaError_t launch_poisson(const double* rho, double* eb, int nx, double dx, cudaStream_t st);
+
+// ---- measured FMA peak (probe.cu) ---------------------------------------------
+cudaError_t fma_peak(int precision, double* ops_per_s, void* sink, cudaStream_t st);
 
 }  // namespace vl

@@ -1,0 +1,669 @@
+// Discrete ten-moment Maxwellian fit by Newton iteration in plain FP64
+// (moment fitting, paper Sec. 2.2 and Algorithm 1): the FP64-mode fit. The
+// FP32 mode uses the double-float kernel of newton.cuh instead.
+//
+// The fit is the one of the double-float kernel and of the oracle: unknowns
+// are the natural parameters eta of M(v) = exp(eta . phi(w)) in scaled
+// coordinates w_a = (v_a - u0_a) / sigma_a (u0 and sigma the targets' mean
+// and standard deviations), the equations D(eta) = sum_c M(v_c) phi(w_c) dv^3
+// = T are the gradient of a convex function whose Hessian is the Gram matrix
+// sum M phi phi^T dv^3, the start and the fallback are the continuous
+// Maxwellian of the targets, and each step is a full Newton step, damped by
+// backtracking on the convex dual L(eta) = D_0 - eta . T while the residual
+// exceeds 1e-6 n (Armijo factor 1e-4, at most 40 halvings).
+//
+// GB300 layout: one warp per cell (every branch of a fit is uniform over its
+// warp). Lane L owns a contiguous run of the N^2 v_x lines of the block.
+// Along a v_x line the exponent is quadratic in the cell index, so M follows
+// the multiplicative recurrence M <- M r, r <- r exp(2 k_xx); line starts
+// follow the same recurrence along v_y and restart (three exponentials) at
+// the lane's first line and at every new v_z plane. The weights are the
+// centred indices c = i - (N-1)/2, which the unrolled line loop holds as
+// constants, so a cell costs five FP64 operations (seven with the Gram
+// sums). Sums are reduced by xor butterflies (identical bits in every lane).
+// The Gram sums of degree <= 4 give the Jacobian through three separable
+// binomial transforms; lane 0 solves the 10 x 10 system by Cholesky.
+// Blocks whose exponent leaves +-700 at a corner of the box, or whose
+// one-cell ratios leave that range, take one exponential per cell instead.
+#pragma once
+
+#include "common.cuh"
+#include "fit_index.cuh"
+#include "kernels.cuh"
+#include "mlp_common.cuh"
+
+namespace vl {
+namespace fit64 {
+namespace {
+
+constexpr int kCoefN = 16;
+constexpr int kCellsPerCta = 4;  // one warp per cell
+
+struct Cell {
+    double eta[10], et[10], eta0[10], T[10], step[10];
+    double m[10];   // index moments of degree <= 2 about the box centre
+    double g[35];   // index moments of degree <= 4 (Gram sums)
+    double k[10];   // index-space exponent of the last evaluation
+    double wc[3], h[3], u0[3], sg[3];
+    double tgt[10];
+};
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// index-space exponent q(c) = k0 + k_a c_a + k_ab c_a c_b of eta, with
+// w_a = wc_a + h_a c_a (c the centred cell indices)
+__device__ __forceinline__ void index_coeffs64(const double* e, const double* wc, const double* h, double* k) {
+    k[0] = e[0] + e[1] * wc[0] + e[2] * wc[1] + e[3] * wc[2] + e[4] * wc[0] * wc[0] + e[5] * wc[0] * wc[1] +
+           e[6] * wc[0] * wc[2] + e[7] * wc[1] * wc[1] + e[8] * wc[1] * wc[2] + e[9] * wc[2] * wc[2];
+    k[1] = h[0] * (e[1] + 2.0 * e[4] * wc[0] + e[5] * wc[1] + e[6] * wc[2]);
+    k[2] = h[1] * (e[2] + 2.0 * e[7] * wc[1] + e[5] * wc[0] + e[8] * wc[2]);
+    k[3] = h[2] * (e[3] + 2.0 * e[9] * wc[2] + e[6] * wc[0] + e[8] * wc[1]);
+    k[4] = e[4] * h[0] * h[0];
+    k[5] = e[5] * h[0] * h[1];
+    k[6] = e[6] * h[0] * h[2];
+    k[7] = e[7] * h[1] * h[1];
+    k[8] = e[8] * h[1] * h[2];
+    k[9] = e[9] * h[2] * h[2];
+}
+
+// Can the recurrences represent every value and one-cell ratio of the block
+// in normal FP64 numbers? The exponent at every corner above -700 (a
+// quadratic with concave diagonal is smallest at a corner; if a diagonal
+// coefficient is not negative the block is refused) and every one-cell
+// difference along x and y, and the ratio multipliers, within +-700
+// (differences are linear in position, extreme at the corners).
+template <int N>
+__device__ bool recurrence_ok(const double* k) {
+    const int l = lane_id() & 7;
+    constexpr double hN = 0.5 * (N - 1);
+    bool ok = k[4] < 0.0 && k[7] < 0.0 && k[9] < 0.0 && fabs(2.0 * k[4]) < 700.0 && fabs(2.0 * k[7]) < 700.0 &&
+              fabs(k[5]) < 700.0;
+    const double x = (l & 1) ? hN : -hN, y = (l & 2) ? hN : -hN, z = (l & 4) ? hN : -hN;
+    const double q = k[0] + k[1] * x + k[2] * y + k[3] * z + k[4] * x * x + k[5] * x * y + k[6] * x * z +
+                     k[7] * y * y + k[8] * y * z + k[9] * z * z;
+    ok = ok && q > -700.0 && q < 700.0;
+    const double dx = k[4] * (2.0 * x + 1.0) + k[1] + k[5] * y + k[6] * z;
+    const double dy = k[7] * (2.0 * y + 1.0) + k[2] + k[5] * x + k[8] * z;
+    ok = ok && fabs(dx) < 700.0 && fabs(dy) < 700.0;
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Gram sums of one line: g[p, q, r] += S_p c_y^q c_z^r
+__device__ __forceinline__ void gram_line64(double* g, const double* S, double cj, double ck) {
+    double pj[5], pk[5];
+    pj[0] = pk[0] = 1.0;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) {
+        pj[q] = pj[q - 1] * cj;
+        pk[q] = pk[q - 1] * ck;
+    }
+#pragma unroll
+    for (int p = 0; p <= 4; ++p)
+#pragma unroll
+        for (int q = 0; q <= 4 - p; ++q)
+#pragma unroll
+            for (int r = 0; r <= 4 - p - q; ++r) g[mono4(p, q, r)] = fma(S[p], pj[q] * pk[r], g[mono4(p, q, r)]);
+}
+
+// Index moments (cs.m; with GRAM also the Gram sums cs.g) of M = exp(q(c))
+// over the block. Returns false if any sum is not finite.
+template <int N, bool GRAM>
+__device__ __noinline__ bool eval64(Cell& cs) {
+    const int lane = lane_id();
+    constexpr double hN = 0.5 * (N - 1);
+    constexpr int NL = N * N;
+    const int l0 = (lane * NL) >> 5, l1 = ((lane + 1) * NL) >> 5;
+    double k[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) k[q] = cs.k[q];
+    double m[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) m[q] = 0.0;
+    double g[GRAM ? 35 : 1];
+#pragma unroll
+    for (int q = 0; q < (GRAM ? 35 : 1); ++q) g[q] = 0.0;
+    if (recurrence_ok<N>(k)) {
+        const double e_in = exp(2.0 * k[4]), e_j = exp(2.0 * k[7]), e_xy = exp(k[5]);
+        double Ms = 0.0, rs = 0.0, rl = 0.0;
+#pragma unroll 1
+        for (int l = l0; l < l1; ++l) {
+            const int j = l % N, kk = l / N;
+            const double cj = j - hN, ck = kk - hN;
+            if (l == l0 || j == 0) {
+                // q along the line: k_xx c^2 + B c + C
+                const double B = k[1] + k[5] * cj + k[6] * ck;
+                const double C = k[0] + k[2] * cj + k[3] * ck + k[7] * cj * cj + k[8] * cj * ck + k[9] * ck * ck;
+                Ms = exp((k[4] * hN - B) * hN + C);
+                rs = exp(k[4] * (2.0 - N) + B);
+                rl = exp(k[2] - k[5] * hN + k[7] * (2.0 * cj + 1.0) + k[8] * ck);
+            }
+            double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            double M = Ms, r = rs;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const double c = i - hN;
+                S[0] += M;
+                S[1] = fma(M, c, S[1]);
+                S[2] = fma(M, c * c, S[2]);
+                if (GRAM) {
+                    S[3] = fma(M, c * c * c, S[3]);
+                    S[4] = fma(M, c * c * c * c, S[4]);
+                }
+                M *= r;
+                r *= e_in;
+            }
+            m[0] += S[0];
+            m[1] += S[1];
+            m[2] = fma(cj, S[0], m[2]);
+            m[3] = fma(ck, S[0], m[3]);
+            m[4] += S[2];
+            m[5] = fma(cj, S[1], m[5]);
+            m[6] = fma(ck, S[1], m[6]);
+            m[7] = fma(cj * cj, S[0], m[7]);
+            m[8] = fma(cj * ck, S[0], m[8]);
+            m[9] = fma(ck * ck, S[0], m[9]);
+            if (GRAM) gram_line64(g, S, cj, ck);
+            Ms *= rl;
+            rl *= e_j;
+            rs *= e_xy;
+        }
+    } else {
+        // one exponential per cell (any exponent range)
+#pragma unroll 1
+        for (int l = l0; l < l1; ++l) {
+            const int j = l % N, kk = l / N;
+            const double cj = j - hN, ck = kk - hN;
+            const double B = k[1] + k[5] * cj + k[6] * ck;
+            const double C = k[0] + k[2] * cj + k[3] * ck + k[7] * cj * cj + k[8] * cj * ck + k[9] * ck * ck;
+            double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+            for (int i = 0; i < N; ++i) {
+                const double c = i - hN;
+                const double M = exp((k[4] * c + B) * c + C);
+                S[0] += M;
+                S[1] = fma(M, c, S[1]);
+                S[2] = fma(M, c * c, S[2]);
+                if (GRAM) {
+                    S[3] = fma(M, c * c * c, S[3]);
+                    S[4] = fma(M, c * c * c * c, S[4]);
+                }
+            }
+            m[0] += S[0];
+            m[1] += S[1];
+            m[2] = fma(cj, S[0], m[2]);
+            m[3] = fma(ck, S[0], m[3]);
+            m[4] += S[2];
+            m[5] = fma(cj, S[1], m[5]);
+            m[6] = fma(ck, S[1], m[6]);
+            m[7] = fma(cj * cj, S[0], m[7]);
+            m[8] = fma(cj * ck, S[0], m[8]);
+            m[9] = fma(ck * ck, S[0], m[9]);
+            if (GRAM) gram_line64(g, S, cj, ck);
+        }
+    }
+    bool fin = true;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        m[q] = warp_allsum(m[q]);
+        fin = fin && isfinite(m[q]);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 10; ++q) cs.m[q] = m[q];
+    if (GRAM) {
+#pragma unroll
+        for (int q = 0; q < 35; ++q) {
+            g[q] = warp_allsum(g[q]);
+            fin = fin && isfinite(g[q]);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 35; ++q) cs.g[q] = g[q];
+    }
+    __syncwarp();
+    return fin;
+}
+
+// evaluation at eta (cs.k set from it); returns whether the sums are finite
+template <int N>
+__device__ __forceinline__ bool evaluate64(Cell& cs, const double* eta, bool gram) {
+    if (lane_id() == 0) index_coeffs64(eta, cs.wc, cs.h, cs.k);
+    __syncwarp();
+    return gram ? eval64<N, true>(cs) : eval64<N, false>(cs);
+}
+
+// w-space moments D (10) from the index moments about the box centre
+__device__ __forceinline__ void w_moments64(const Cell& cs, double vol, double* D) {
+    const double* m = cs.m;
+    const double* w = cs.wc;
+    const double* h = cs.h;
+    D[0] = m[0];
+    D[1] = w[0] * m[0] + h[0] * m[1];
+    D[2] = w[1] * m[0] + h[1] * m[2];
+    D[3] = w[2] * m[0] + h[2] * m[3];
+    D[4] = w[0] * w[0] * m[0] + 2.0 * w[0] * h[0] * m[1] + h[0] * h[0] * m[4];
+    D[5] = w[0] * w[1] * m[0] + w[0] * h[1] * m[2] + h[0] * w[1] * m[1] + h[0] * h[1] * m[5];
+    D[6] = w[0] * w[2] * m[0] + w[0] * h[2] * m[3] + h[0] * w[2] * m[1] + h[0] * h[2] * m[6];
+    D[7] = w[1] * w[1] * m[0] + 2.0 * w[1] * h[1] * m[2] + h[1] * h[1] * m[7];
+    D[8] = w[1] * w[2] * m[0] + w[1] * h[2] * m[3] + h[1] * w[2] * m[2] + h[1] * h[2] * m[8];
+    D[9] = w[2] * w[2] * m[0] + 2.0 * w[2] * h[2] * m[3] + h[2] * h[2] * m[9];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) D[q] *= vol;
+}
+
+// coefficients C(A, p) w^(A-p) h^p of (w + h c)^A, packed by tri(A, p)
+__device__ __forceinline__ void binom_coeffs64(double w, double h, double* c) {
+    double pw[5], ph[5];
+    pw[0] = ph[0] = 1.0;
+#pragma unroll
+    for (int e = 1; e < 5; ++e) {
+        pw[e] = pw[e - 1] * w;
+        ph[e] = ph[e - 1] * h;
+    }
+#pragma unroll
+    for (int A = 0; A <= 4; ++A)
+#pragma unroll
+        for (int p = 0; p <= A; ++p) c[tri(A, p)] = (double)binom4(A, p) * pw[A - p] * ph[p];
+}
+
+// Newton direction: the Gram matrix in w-space from the index sums (three
+// separable binomial transforms), Cholesky, J step = -G. Lane 0; returns
+// (to every lane) whether J was positive definite.
+__device__ __noinline__ bool newton_step64(Cell& cs, const double* G, double vol) {
+    int ok = 1;
+    if (lane_id() == 0) {
+        double cx[15], cy[15], cz[15], U[35], W[35];
+        binom_coeffs64(cs.wc[0], cs.h[0], cx);
+        binom_coeffs64(cs.wc[1], cs.h[1], cy);
+        binom_coeffs64(cs.wc[2], cs.h[2], cz);
+        const double* g = cs.g;
+#pragma unroll
+        for (int A = 0; A <= 4; ++A)
+#pragma unroll
+            for (int q = 0; q <= 4 - A; ++q)
+#pragma unroll
+                for (int r = 0; r <= 4 - A - q; ++r) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int p = 0; p <= A; ++p) s = fma(cx[tri(A, p)], g[mono4(p, q, r)], s);
+                    U[mono4(A, q, r)] = s;
+                }
+#pragma unroll
+        for (int A = 0; A <= 4; ++A)
+#pragma unroll
+            for (int B = 0; B <= 4 - A; ++B)
+#pragma unroll
+                for (int r = 0; r <= 4 - A - B; ++r) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int q = 0; q <= B; ++q) s = fma(cy[tri(B, q)], U[mono4(A, q, r)], s);
+                    W[mono4(A, B, r)] = s;
+                }
+#pragma unroll
+        for (int A = 0; A <= 4; ++A)
+#pragma unroll
+            for (int B = 0; B <= 4 - A; ++B)
+#pragma unroll
+                for (int C = 0; C <= 4 - A - B; ++C) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int r = 0; r <= C; ++r) s = fma(cz[tri(C, r)], W[mono4(A, B, r)], s);
+                    U[mono4(A, B, C)] = s * vol;
+                }
+        double J[55], inv[10];
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b)
+                J[tri(a, b)] = U[mono4(expo(a, 0) + expo(b, 0), expo(a, 1) + expo(b, 1), expo(a, 2) + expo(b, 2))];
+#pragma unroll
+        for (int i = 0; i < 10; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                double s = J[tri(i, j)];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s = fma(-J[tri(i, q)], J[tri(j, q)], s);
+                if (i == j) {
+                    ok &= s > 0.0 ? 1 : 0;
+                    const double d = sqrt(fmax(s, 1e-300));
+                    J[tri(i, i)] = d;
+                    inv[i] = 1.0 / d;
+                } else {
+                    J[tri(i, j)] = s * inv[j];
+                }
+            }
+        double y[10];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) {
+            double s = -G[i];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s = fma(-J[tri(i, q)], y[q], s);
+            y[i] = s * inv[i];
+        }
+#pragma unroll
+        for (int i = 9; i >= 0; --i) {
+            double s = y[i];
+#pragma unroll
+            for (int q = i + 1; q < 10; ++q) s = fma(-J[tri(q, i)], y[q], s);
+            y[i] = s * inv[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 10; ++i) cs.step[i] = y[i];
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Fit set-up (lane 0, targets in cs.tgt): scaled coordinates, w-space
+// targets T = (n, 0, n Corr) and the continuous Maxwellian eta0. Returns
+// (to every lane) false for invalid targets (n <= 0 or not finite, Theta not
+// positive definite).
+template <int N>
+__device__ __noinline__ bool setup64(Cell& cs, const FitArgs& a) {
+    int ok = 0;
+    if (lane_id() == 0) {
+        const double* t = cs.tgt;
+        const double n = t[0];
+        if (n > 0.0 && isfinite(n)) {
+            double u0[3], Th[9];
+            for (int q = 0; q < 3; ++q) u0[q] = t[1 + q] / n;
+            const int pk[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) Th[p * 3 + q] = t[pk[p][q]] / n - u0[p] * u0[q];
+            // positive definite (Cholesky)
+            bool pd = Th[0] > 0.0;
+            double l00 = 0, l10 = 0, l20 = 0, l11 = 0, l21 = 0;
+            if (pd) {
+                l00 = sqrt(Th[0]);
+                l10 = Th[3] / l00;
+                l20 = Th[6] / l00;
+                const double d1 = Th[4] - l10 * l10;
+                pd = d1 > 0.0;
+                if (pd) {
+                    l11 = sqrt(d1);
+                    l21 = (Th[7] - l20 * l10) / l11;
+                    pd = Th[8] - l20 * l20 - l21 * l21 > 0.0;
+                }
+            }
+            bool fin = true;
+            for (int q = 0; q < 10; ++q) fin = fin && isfinite(t[q]);
+            if (pd && fin) {
+                double sg[3], Cr[9];
+                for (int q = 0; q < 3; ++q) sg[q] = sqrt(Th[q * 4]);
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q) Cr[p * 3 + q] = Th[p * 3 + q] / (sg[p] * sg[q]);
+                for (int q = 0; q < 3; ++q) {
+                    cs.u0[q] = u0[q];
+                    cs.sg[q] = sg[q];
+                    cs.h[q] = a.dv[q] / sg[q];
+                    cs.wc[q] = (a.vmin[q] + 0.5 * N * a.dv[q] - u0[q]) / sg[q];
+                }
+                cs.T[0] = n;
+                cs.T[1] = cs.T[2] = cs.T[3] = 0.0;
+                cs.T[4] = n * Cr[0];
+                cs.T[5] = n * Cr[1];
+                cs.T[6] = n * Cr[2];
+                cs.T[7] = n * Cr[4];
+                cs.T[8] = n * Cr[5];
+                cs.T[9] = n * Cr[8];
+                // P = Corr^-1
+                const double c00 = Cr[4] * Cr[8] - Cr[5] * Cr[7], c01 = Cr[5] * Cr[6] - Cr[3] * Cr[8],
+                             c02 = Cr[3] * Cr[7] - Cr[4] * Cr[6];
+                const double id = 1.0 / (Cr[0] * c00 + Cr[1] * c01 + Cr[2] * c02);
+                const double P00 = c00 * id, P01 = (Cr[2] * Cr[7] - Cr[1] * Cr[8]) * id,
+                             P02 = (Cr[1] * Cr[5] - Cr[2] * Cr[4]) * id, P11 = (Cr[0] * Cr[8] - Cr[2] * Cr[6]) * id,
+                             P12 = (Cr[2] * Cr[3] - Cr[0] * Cr[5]) * id, P22 = (Cr[0] * Cr[4] - Cr[1] * Cr[3]) * id;
+                const double detTh = Th[0] * (Th[4] * Th[8] - Th[5] * Th[7]) - Th[1] * (Th[3] * Th[8] - Th[5] * Th[6]) +
+                                     Th[2] * (Th[3] * Th[7] - Th[4] * Th[6]);
+                cs.eta0[0] = log(n) - 1.5 * log(2.0 * 3.14159265358979323846) - 0.5 * log(detTh);
+                cs.eta0[1] = cs.eta0[2] = cs.eta0[3] = 0.0;
+                cs.eta0[4] = -0.5 * P00;
+                cs.eta0[5] = -P01;
+                cs.eta0[6] = -P02;
+                cs.eta0[7] = -0.5 * P11;
+                cs.eta0[8] = -P12;
+                cs.eta0[9] = -0.5 * P22;
+                ok = 1;
+            }
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// the fitted exponent must be a Gaussian: -2 mu positive definite
+__device__ __forceinline__ bool gaussian64(const double* e) {
+    const double a00 = -2.0 * e[4], a10 = -e[5], a20 = -e[6], a11 = -2.0 * e[7], a21 = -e[8], a22 = -2.0 * e[9];
+    if (!(a00 > 0.0)) return false;
+    const double l00 = sqrt(a00), l10 = a10 / l00, l20 = a20 / l00, d1 = a11 - l10 * l10;
+    if (!(d1 > 0.0)) return false;
+    const double l11 = sqrt(d1), l21 = (a21 - l20 * l10) / l11;
+    return a22 - l20 * l20 - l21 * l21 > 0.0;
+}
+
+struct Work64 {
+    unsigned m, g, warm;
+};
+
+// Newton iteration from cs.eta (uniform over the warp). Returns whether the
+// residual reached tol n and the fitted exponent is a Gaussian; *iters gets
+// the number of Newton steps.
+template <int N>
+__device__ __noinline__ bool newton64(Cell& cs, const FitArgs& a, double n, double vol, int* iters, Work64& work) {
+    const int lane = lane_id();
+    const double tol = a.tol * n;
+    bool haveD = false, haveG = false, gram_next = true, converged = false;
+    int it = 0;
+    for (it = 0;; ++it) {
+        if (!haveD) {
+            evaluate64<N>(cs, cs.eta, gram_next);
+            work.m += 1u;
+            work.g += gram_next ? 1u : 0u;
+            haveD = true;
+            haveG = gram_next;
+        }
+        double D[10], G[10];
+        w_moments64(cs, vol, D);
+        double gmax = 0.0;
+        bool fin = true;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            G[q] = D[q] - cs.T[q];
+            fin = fin && isfinite(G[q]);
+            gmax = fmax(gmax, fabs(G[q]));
+        }
+        if (fin && gmax <= tol) {
+            converged = true;
+            break;
+        }
+        if (!fin || it == a.max_iter) break;
+        if (!haveG) {
+            // the Jacobian at eta (the moments come out the same)
+            evaluate64<N>(cs, cs.eta, true);
+            work.m += 1u;
+            work.g += 1u;
+            haveG = true;
+        }
+        if (!newton_step64(cs, G, vol)) break;
+        const double rel = gmax / n;
+        // Gram sums with the next evaluation where another step is likely
+        // (the residual after a Newton step falls roughly as its square)
+        gram_next = 100.0 * rel * rel > a.tol;
+        if (gmax > 1e-6 * n) {
+            double L0 = D[0], gd = 0.0;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) {
+                L0 -= cs.eta[q] * cs.T[q];
+                gd += G[q] * cs.step[q];
+            }
+            double lam = 1.0;
+            bool accepted = false;
+            for (int ls = 0; ls < 40; ++ls) {
+                if (lane < 10) cs.et[lane] = cs.eta[lane] + lam * cs.step[lane];
+                __syncwarp();
+                const bool ef = evaluate64<N>(cs, cs.et, gram_next);
+                work.m += 1u;
+                work.g += gram_next ? 1u : 0u;
+                double L1 = cs.m[0] * vol;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) L1 -= cs.et[q] * cs.T[q];
+                if (ef && isfinite(L1) && L1 <= L0 + 1e-4 * lam * gd) {
+                    accepted = true;
+                    break;
+                }
+                lam *= 0.5;
+            }
+            if (lane < 10) cs.eta[lane] = accepted ? cs.et[lane] : cs.eta[lane] + lam * cs.step[lane];
+            __syncwarp();
+            haveD = accepted;
+            haveG = accepted && gram_next;
+        } else {
+            if (lane < 10) cs.eta[lane] = cs.eta[lane] + cs.step[lane];
+            __syncwarp();
+            haveD = false;
+            haveG = false;
+        }
+    }
+    *iters = it;
+    return converged && gaussian64(cs.eta);
+}
+
+// non-finite or negative targets (a numeric error upstream); empty cells
+// (n = 0) are not
+__device__ __forceinline__ bool bad_targets(const double* t, int n) {
+    bool bad = !(t[0] >= 0.0);
+    for (int q = 0; q < n; ++q) bad = bad || !isfinite(t[q]);
+    return bad;
+}
+
+// One fit by a warp: from the network's prediction when warm is not null
+// (then from the cold start if that run fails), else from the continuous
+// Maxwellian. Writes the coefficients (eta, u0, sigma) to coef, appends a
+// training sample of a converged fit when harvesting; returns 0 converged,
+// 1 fallback (continuous Maxwellian), 2 invalid targets.
+template <int N>
+__device__ int fit_cell64(Cell& cs, const FitArgs& a, double* coef, const float* warm, int* iters, Work64& work) {
+    const int lane = lane_id();
+    *iters = 0;
+    if (!setup64<N>(cs, a)) {
+        if (lane < kCoefN) coef[lane] = 0.0;
+        return 2;
+    }
+    const double n = cs.tgt[0];
+    const double vol = a.dv[0] * a.dv[1] * a.dv[2];
+    bool good = false;
+    // the guard of the network's inference writes NaN rows for the fits it rejects
+    if (warm && warm[0] == warm[0] && fabsf(warm[0]) < 1e30f) work.warm += 1u;
+    if (warm) {
+        if (lane < 10) {
+            const float dw = warm[lane];
+            cs.eta[lane] = cs.eta0[lane] + ((dw == dw && fabsf(dw) < 1e30f) ? (double)dw : 0.0);
+        }
+        __syncwarp();
+        good = newton64<N>(cs, a, n, vol, iters, work);
+    }
+    if (!good) {
+        if (lane < 10) cs.eta[lane] = cs.eta0[lane];
+        __syncwarp();
+        int it2 = 0;
+        good = newton64<N>(cs, a, n, vol, &it2, work);
+        *iters += it2;
+    }
+    if (lane < 10) coef[lane] = good ? cs.eta[lane] : cs.eta0[lane];
+    else if (lane < 13) coef[lane] = cs.u0[lane - 10];
+    else if (lane < 16) coef[lane] = cs.sg[lane - 13];
+    if (good && a.harvest) {
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd(a.harvest_count, 1ull);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot < (unsigned long long)a.harvest_cap) {
+            float* smp = a.harvest + slot * mlp::kSample;
+            if (lane == 0) {
+                float x[mlp::kIn];
+                const bool ok = mlp::fit_inputs(cs.tgt, a.vmin, a.dv, a.vmax, x);
+                for (int q = 0; q < mlp::kIn; ++q) smp[q] = x[q];
+                smp[22] = ok ? 1.f : 0.f;
+                smp[23] = 0.f;
+            }
+            if (lane < 10) smp[mlp::kIn + lane] = (float)(cs.eta[lane] - cs.eta0[lane]);
+        }
+    }
+    __syncwarp();
+    return good ? 0 : 1;
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * kCellsPerCta) newton64_kernel(FitArgs a) {
+    __shared__ Cell cells[kCellsPerCta];
+    __shared__ unsigned long long cnt[VL_NSTATS];
+    if (threadIdx.x < VL_NSTATS) cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int lane = lane_id();
+    const int slot = threadIdx.x >> 5;
+    Cell& cs = cells[slot];
+    for (long long cell = (long long)blockIdx.x * kCellsPerCta + slot; cell < a.ncell;
+         cell += (long long)gridDim.x * kCellsPerCta) {
+        // V targets: the moments of f
+        if (lane < 10) cs.tgt[lane] = a.vmom[cell * 20 + lane];
+        __syncwarp();
+        bool bad = lane == 0 && bad_targets(cs.tgt, 10);
+        const double nV = cs.tgt[0];
+        Work64 work = {0u, 0u, 0u};
+        int itv = 0, itf = 0;
+        const float* wv = a.warm ? a.warm + cell * 20 : nullptr;
+        const int stv = fit_cell64<N>(cs, a, a.coef_v + cell * kCoefN, wv, &itv, work);
+        // F targets: the fluid moments rescaled by n_V / n_F
+        const double nF = a.fluid[cell * 10];
+        if (lane == 0) {
+            double raw[10];
+            for (int q = 0; q < 10; ++q) raw[q] = a.fluid[cell * 10 + q];
+            bad = bad || bad_targets(raw, 10);
+        }
+        const double scale = nF > 0.0 ? nV / nF : 0.0;
+        __syncwarp();
+        if (lane < 10) {
+            cs.tgt[lane] = a.fluid[cell * 10 + lane] * scale;
+        }
+        __syncwarp();
+        if (lane < 10) a.fluid[cell * 10 + lane] = cs.tgt[lane];
+        const float* wf = a.warm ? a.warm + cell * 20 + 10 : nullptr;
+        const int stf = fit_cell64<N>(cs, a, a.coef_f + cell * kCoefN, wf, &itf, work);
+        if (lane == 0) {
+            a.status[cell * 2] = stv;
+            a.status[cell * 2 + 1] = stf;
+            if (bad && a.numeric) *reinterpret_cast<volatile int*>(a.numeric) = VL_ENUMERIC;
+            atomicAdd_block(&cnt[CNT_ITERS], (unsigned long long)(itv + itf));
+            const unsigned long long fb = (stv == 1) + (stf == 1);
+            if (fb) atomicAdd_block(&cnt[CNT_FALLBACK], fb);
+            const unsigned long long inv = (stv == 2) + (stf == 2);
+            if (inv) atomicAdd_block(&cnt[CNT_INVALID], inv);
+            atomicAdd_block(&cnt[CNT_EVAL64_M], (unsigned long long)work.m);
+            atomicAdd_block(&cnt[CNT_EVAL64_G], (unsigned long long)work.g);
+            if (work.warm) atomicAdd_block(&cnt[CNT_WARM], (unsigned long long)work.warm);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < VL_NSTATS && threadIdx.x != CNT_CLIPPED && cnt[threadIdx.x])
+        atomicAdd(&a.counters[threadIdx.x], cnt[threadIdx.x]);
+}
+
+template <int N>
+cudaError_t launch64(const FitArgs& a, cudaStream_t st) {
+    long long blocks = (a.ncell + kCellsPerCta - 1) / kCellsPerCta;
+    if (blocks > 0x7FFFFFFFLL) blocks = 0x7FFFFFFFLL;
+    if (blocks < 1) return cudaSuccess;
+    newton64_kernel<N><<<(unsigned)blocks, 32 * kCellsPerCta, 0, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace fit64
+}  // namespace vl

@@ -1,6 +1,9 @@
-// Newton fit kernel for 16^3 velocity blocks (see newton.cuh).
+// Newton fit kernels for 16^3 velocity blocks: double-float (newton.cuh)
+// and FP64 (newton64.cuh).
 #include "newton.cuh"
+#include "newton64.cuh"
 
 namespace vl {
 cudaError_t launch_newton_16(const FitArgs& a, cudaStream_t st) { return launch_n<16>(a, st); }
+cudaError_t launch_newton64_16(const FitArgs& a, cudaStream_t st) { return fit64::launch64<16>(a, st); }
 }  // namespace vl

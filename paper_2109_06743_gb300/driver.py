@@ -25,9 +25,11 @@ from . import abi
 class Simulation:
     def __init__(self, cfg, f_list, fluid_list=None, yee=None, device="cuda", stream=None, fit=True,
                  fused_xy=True, wide_fit=None):
-        """wide_fit: the Newton kernel with the centre-out evaluation for
-        Maxwellians narrow against their velocity box (moment_fit_wide), per
-        species; None decides from the initial moments (see wide_species)."""
+        """wide_fit: which double-float Newton kernel the FP32-mode fits use
+        (moment_fit_wide): None lets the library choose it on the device at
+        every fit from the targets; True/False forces the kernel with the
+        centre-out evaluation (Maxwellians narrow against their velocity box)
+        or the common one for every species."""
         import torch
 
         self.torch = torch
@@ -80,41 +82,11 @@ class Simulation:
             abi.maxwell_step(self.ctx, 0.0, None, s)  # cell-centred fields of the initial Yee fields
         else:
             abi.maxwell_step(self.ctx, 0.0, self.mom_t, s)
-        self.wide = [False] * len(cfg.species)
-        if nvdim == 3 and fit:
-            want = self.wide_species() if wide_fit is None else [bool(wide_fit)] * len(cfg.species)
-            for k, w in enumerate(want):
-                abi.moment_fit_wide(self.ctx, k, w)
-                self.wide[k] = w
+        self.wide_fit = wide_fit
+        if nvdim == 3 and fit and wide_fit is not None:
+            for k in range(len(cfg.species)):
+                abi.moment_fit_wide(self.ctx, k, wide_fit)
         self.time = 0.0
-
-    # spread (decrease of the exponent from a cell's Maxwellian peak to the
-    # farthest box corner) above which a species takes the wide fit kernel:
-    # the common evaluation needs every value of the block within e^+-80,
-    # and the peak itself lies some e-folds below 1
-    WIDE_SPREAD = 60.0
-
-    def wide_species(self):
-        """Per species, whether some cell's Maxwellian (from the current
-        moments of f) falls by more than WIDE_SPREAD e-folds from its peak to
-        the farthest corner of the velocity box; cells whose density is below
-        1e-10 of the species' largest (whose fits are not valid anyway) are
-        left out."""
-        torch = self.torch
-        out = []
-        for sp, m in zip(self.cfg.species, self.mom_t):
-            with torch.cuda.stream(self.stream):
-                n = m[:, 0].clamp_min(1e-300)
-                spread = torch.zeros_like(n)
-                for a, d in enumerate((4, 7, 9)):
-                    u = m[:, 1 + a] / n
-                    th = (m[:, d] / n - u * u).clamp_min(1e-300)
-                    ext = torch.maximum(sp.vmax[a] - u, u - sp.vmin[a])
-                    spread = spread + ext * ext / (2.0 * th)
-                live = m[:, 0] > 1e-10 * m[:, 0].max()
-                big = bool(((spread > self.WIDE_SPREAD) & live).any().item())
-            out.append(big)
-        return out
 
     def close(self):
         if self.ctx is not None:

@@ -71,3 +71,35 @@ def test_host_only_calls_reject_a_missing_context(lib):
     """moment_fit_wide is host-only: without a context it returns VL_EINVAL
     (1) and launches nothing."""
     assert lib.moment_fit_wide(None, 0, 1) == 1
+
+
+def test_static_pass_refuses_bad_pointers_before_any_launch(lib):
+    """pfc_advect_v_static checks its raw pointers on the host: a pointer not
+    aligned to its element size (f) or to 8 bytes (E and B, moments), or
+    moments that overlap f, return VL_EINVAL (1) before the scratch address
+    is looked up or anything is launched (the addresses here are never
+    dereferenced)."""
+    cfg = W.harris(nx=4, ny=4, nv=8, lx=0.8, ly=0.8, precision=32)
+    d = abi.make_desc(cfg)
+    D = abi.ctypes.byref(d)
+    V = 8 ** 3
+    base = 1 << 40
+    eb = base + (1 << 30)
+    mom = base + (2 << 30)
+    cases = [
+        (base + 2, eb, mom, b"f_dev is not aligned"),
+        (base, eb + 4, mom, b"eb_dev is not 8-byte aligned"),
+        (base, eb, mom + 4, b"mom_out is not 8-byte aligned"),
+        (base, eb, base + 8 * V * 4, b"mom_out overlaps f_dev"),
+    ]
+    for f, e, m, msg in cases:
+        assert lib.pfc_advect_v_static(D, 0, f, e, 16, 0.01, m, None) == abi.VL_EINVAL
+        assert msg in lib.vl_last_error(None), lib.vl_last_error(None)
+    d64 = abi.make_desc(cfg)
+    d64.precision = 64
+    assert lib.pfc_advect_v_static(abi.ctypes.byref(d64), 0, base + 4, eb, 16, 0.01, None, None) == abi.VL_EINVAL
+    assert b"f_dev is not aligned" in lib.vl_last_error(None)
+
+
+def test_sync_status_rejects_a_missing_context(lib):
+    assert lib.vl_sync_status(None, None) == abi.VL_EINVAL

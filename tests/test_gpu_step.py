@@ -52,7 +52,6 @@ def test_fp64_steps_match_oracle(gpu, orc, kind):
         f, yee = W.wave2d_state(cfg), W.wave2d_yee(cfg)
     cfg.fit_tol = 1e-12
     ost, sim = run_both(cfg, f, yee, 3)
-    assert sim.wide == [False, False]  # boxes of +-5 thermal speeds: the common fit kernel
     for k in range(2):
         ref = ost.f[k]
         got = sim.f_host(k)
@@ -62,6 +61,8 @@ def test_fp64_steps_match_oracle(gpu, orc, kind):
     np.testing.assert_allclose(sim.yee.cpu().numpy(), ost.yee, rtol=0, atol=1e-10 * np.abs(ost.yee).max())
     st = sim.stats()
     assert st[1] == 0 and st[3] == 0
+    # FP64 mode: every fit by the plain FP64 kernel
+    assert st[10] > 0 and st[4] == 0 and st[9] == 0, st
     sim.close()
 
 
