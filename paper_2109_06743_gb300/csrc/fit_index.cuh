@@ -28,6 +28,12 @@ __host__ __device__ constexpr int expo(int a, int axis) {
          : a == 8 ? (axis >= 1 ? 1 : 0)
          : (axis == 2 ? 2 : 0);
 }
+// packed index of (p, q), p + q <= 4 (by q, then p)
+__host__ __device__ constexpr int tri4(int p, int q) {
+    int idx = 0;
+    for (int e = 0; e < q; ++e) idx += 5 - e;
+    return idx + p;
+}
 // C(n, k) for n <= 4
 __host__ __device__ constexpr int binom4(int n, int k) {
     return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : (k == 1 || k == n - 1) ? n : 6;
