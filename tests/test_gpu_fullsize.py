@@ -15,7 +15,15 @@ outputs one by one:
 * fit: the fitted parameters of sampled cells (V and the rescaled F targets)
   equal the oracle's fits of the same targets to 1e-8;
 * exchange: sampled blocks after the exchange equal the oracle's moment fit
-  and exchange of the same block and fluid state within 2e-5 of max f.
+  and exchange of the same block and fluid state within 2e-5 of max f;
+* the fused sweep's edge tiles: samples in the four columns next to the
+  periodic seam in x, and samples in the four rows next to either wall,
+  whose oracle value comes from the oracle's PFC lines along x of the
+  twelve rows next to the wall (the sampled velocity column and its v_y
+  mirror) followed by the oracle's walled y sweep of those rows;
+* the warm-started fit (use_mlp = 1, the benchmark's timed form) with a
+  network trained as in the benchmark: fitted parameters of sampled cells
+  equal the oracle's fits of the same targets to 1e-8.
 """
 import math
 
@@ -66,8 +74,10 @@ def test_full_size_passes_match_the_oracle_on_samples(gpu, orc, name):
         fin4 = fin.view(cfg.ny, cfg.nx, V)
         fmax = fin.max().item()
         vx, vy = sp.vcentres(0), sp.vcentres(1)
-        for _ in range(6):
-            y, x, vi = int(rng.integers(8, cfg.ny - 8)), int(rng.integers(0, cfg.nx)), int(rng.integers(0, V))
+        for n_s in range(10):
+            y, vi = int(rng.integers(8, cfg.ny - 8)), int(rng.integers(0, V))
+            # the last four samples sit on the periodic seam in x
+            x = int(rng.integers(0, cfg.nx)) if n_s < 6 else [0, 1, cfg.nx - 2, cfg.nx - 1][n_s - 6]
             ix, iy = vi % nv, (vi // nv) % nv
             cx, cy = vx[ix] * dt / cfg.dx, vy[iy] * dt / cfg.dy
             assert abs(cx) < 1 and abs(cy) < 1
@@ -76,6 +86,28 @@ def test_full_size_passes_match_the_oracle_on_samples(gpu, orc, name):
             want = orc.pfc_line(xs, 1, 4, cy)[0]
             got = fout.view(cfg.ny, cfg.nx, V)[y, x, vi].item()
             assert abs(got - want) <= 4e-6 * fmax, (k, y, x, vi, got, want)
+        # rows next to the walls: x sweeps of the 12 rows nearest the wall for
+        # the sampled column and its v_y mirror (the wall's ghost column), then
+        # the oracle's walled y sweep of those rows
+        gw = orc.make_grid(3, 1, 12, 0.0, cfg.dx, 0.0, cfg.dy, 1)
+        for n_s in range(4):
+            x, vi = int(rng.integers(0, cfg.nx)), int(rng.integers(0, V))
+            ix, iy, iz = vi % nv, (vi // nv) % nv, vi // (nv * nv)
+            vm = (iz * nv + (nv - 1 - iy)) * nv + ix
+            cx = vx[ix] * dt / cfg.dx
+            top = n_s % 2 == 1
+            rows = list(range(cfg.ny - 12, cfg.ny)) if top else list(range(12))
+            sub = np.zeros((12, V))
+            for col in (vi, vm):
+                lines = fin4[rows[0]:rows[-1] + 1, :, col].double().cpu().numpy()
+                for jr, r in enumerate(lines):
+                    sub[jr, col] = orc.pfc_line(np.concatenate([r[-4:], r, r[:4]]), cfg.nx, 4, cx)[x]
+            # the sub-grid has walls at both ends; only the one next to the
+            # checked rows is the workload's
+            orc.advect_space(sub, gw, s1, 1, dt)
+            for jr in ((8, 9, 10, 11) if top else (0, 1, 2, 3)):
+                got = fout.view(cfg.ny, cfg.nx, V)[rows[jr], x, vi].item()
+                assert abs(got - sub[jr, vi]) <= 4e-6 * fmax, (k, rows[jr], x, vi, got, sub[jr, vi])
         # ---- velocity pass with fused moments --------------------------------
         cells = rng.integers(0, cfg.ncell, 6)
         ct = torch.as_tensor(cells, device=sim.dev)
@@ -132,6 +164,28 @@ def test_full_size_passes_match_the_oracle_on_samples(gpu, orc, name):
     # sheet (boxes sized for its hot side), the common one for the Harris
     # sheet; no FP64-exponential evaluations either way
     assert st[9] == (2 * cfg.ncell if cfg.kind == "asym" else 0) * 2 and st[6] == 0, st
+    # ---- the warm-started fit (use_mlp = 1, the benchmark's timed form) -------
+    from paper_2109_06743_gb300.warmstart import train_warm_start
+    w, _ = train_warm_start(W.TRAIN_FROM[name], sim.dev)
+    abi.mlp_set_weights(ctx, w)
+    abi.vl_reset_stats(ctx, s)
+    for k, sp in enumerate(cfg.species):
+        s1 = orc.make_species(sp.q, sp.m, sp.nv, sp.vmin, sp.vmax)
+        cells = rng.integers(0, cfg.ncell, 4)
+        ct = torch.as_tensor(cells, device=sim.dev)
+        thv = torch.zeros((cfg.ncell, 10), dtype=torch.float64, device=sim.dev)
+        thf = torch.zeros_like(thv)
+        abi.moment_fit_solve(ctx, k, sim.mom_t1[k], True, thv, thf, s)
+        torch.cuda.synchronize()
+        vm = sim.mom_t1[k][ct].cpu().numpy()
+        fl = sim.fluid[k][ct].cpu().numpy()
+        for j, c in enumerate(cells):
+            for targets, th_gpu in ((vm[j, :10], thv[c]), (fl[j], thf[c])):
+                th, it, st_ = orc.maxent_fit(np.ascontiguousarray(targets), s1, 3, cfg.fit_tol, cfg.fit_max_iter)
+                assert st_ == 0
+                np.testing.assert_allclose(th_gpu.cpu().numpy(), th, rtol=1e-8, atol=1e-12 * abs(th).max())
+    st = abi.vl_read_stats(ctx, s)
+    assert st[12] > 0.9 * 2 * cfg.ncell * len(cfg.species) and st[1] == 0, st  # started from the network
     sim.close()
 
 

@@ -99,3 +99,55 @@ def test_static_scratch_split_ranges_and_limit(gpu):
     # an empty range is a no-op
     abi.pfc_advect_v_static(r.desc, s, f_b, r.eb, 0, dt, None, stream=r.stream)
     r.close()
+
+
+def test_static_scratch_1d1v_matches_workspace_pass(gpu):
+    """The 1D1V branch of the allocation-free pass (one thread per spatial
+    cell, E read at stride 6) against pfc_advect_v on the Landau set-up,
+    two calls in a row."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    torch = gpu
+    cfg = W.landau()
+    f0 = W.landau_state(cfg)
+    eb = np.zeros((cfg.ncell, 6))
+    eb[:, 0] = 0.3 * np.sin(np.linspace(0.0, 2.0 * np.pi, cfg.ncell, endpoint=False))
+    eb[:, 1:] = 7.0  # other components must not be read
+    r = AbiRunner(cfg, f0, eb=eb)
+    f_b = r.f[0].clone()
+    for dt in (0.05, -0.03):
+        m_a, m_b = r.mom(), r.mom()
+        abi.pfc_advect_v(r.ctx, 0, dt, m_a, stream=r.stream)
+        abi.pfc_advect_v_static(r.desc, 0, f_b, r.eb, cfg.ncell, dt, m_b, stream=r.stream)
+        torch.cuda.synchronize()
+        fa = r.f[0].cpu().numpy()
+        _close(fa, f_b.cpu().numpy(), 64, fa.max())
+        ma = m_a.cpu().numpy()
+        _close(ma, m_b.cpu().numpy(), 64, np.abs(ma).max(axis=0, keepdims=True) + 1e-300)
+    r.close()
+
+
+def test_static_scratch_full_array(gpu):
+    """One FP32 8^3 call over exactly VL_STATIC_SCRATCH_CELLS cells (the whole
+    static array, 67 MB of f) against the workspace pass of the same cells."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    torch = gpu
+    n = abi.STATIC_SCRATCH_CELLS
+    cfg = W.harris(nx=256, ny=n // 256, nv=8, lx=25.6 * 2, ly=12.8 * (n // 256) / 64, precision=32)
+    assert cfg.ncell == n
+    V = 8 ** 3
+    f0 = [W.random_blocks((n, V), 31 + k, dtype=np.float32) ** 4 for k in range(2)]
+    eb = W.random_fields(n, 37, e_scale=0.5, b_scale=1.0)
+    r = AbiRunner(cfg, f0, eb=eb)
+    s = 0
+    f_b = r.f[s].clone()
+    m_a, m_b = r.mom(), r.mom()
+    abi.pfc_advect_v(r.ctx, s, 0.02, m_a, stream=r.stream)
+    abi.pfc_advect_v_static(r.desc, s, f_b, r.eb, n, 0.02, m_b, stream=r.stream)
+    torch.cuda.synchronize()
+    fa = r.f[s].double().cpu().numpy()
+    _close(fa, f_b.double().cpu().numpy(), 32, fa.max())
+    ma = m_a.cpu().numpy()
+    _close(ma, m_b.cpu().numpy(), 32, np.abs(ma).max(axis=0, keepdims=True) + 1e-300)
+    r.close()
