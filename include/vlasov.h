@@ -234,6 +234,16 @@ vl_status moment_fit_wide(vl_ctx* ctx, int species, int wide);
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t,
                      const double* const* mom_t1, vl_stream_t stream);
 
+/* fluid_step for species s alone (its raw moments mom_t, mom_t1). Each
+ * species' fluid state evolves with its own moments and the frozen fields,
+ * so the species may be stepped separately, in any order: a caller can run
+ * one species' fluid step, fit and exchange before the next species' sweeps
+ * (and start moving its f while the next species computes). Uses the
+ * workspace's fluid stage buffers, so calls for different species on
+ * different streams must not overlap. */
+vl_status fluid_step_species(vl_ctx* ctx, int species, double dt, const double* mom_t,
+                             const double* mom_t1, vl_stream_t stream);
+
 /* The stand-alone ten-moment fluid model with the gradient heat-flux closure
  * (Sec. 2.3, Eq. "gradient closure"): one SSP-RK3 step of length dt of every
  * species' fluid state, E and B frozen at the context's cell-centred fields.

@@ -18,7 +18,7 @@ NSTATS = 13  # VL_NSTATS
 VL_OK, VL_EINVAL, VL_ECUDA, VL_ENOCONV, VL_ENUMERIC, VL_ENOTSUP = range(6)
 
 EXPORTED = ["vlasov_work_bytes", "vlasov_init", "vlasov_free", "vl_last_error", "pfc_advect_x",
-            "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "moment_fit_wide", "fluid_step",
+            "pfc_advect_xy", "pfc_advect_v", "pfc_advect_v_static", "moments", "moment_fit", "moment_fit_solve", "moment_fit_exchange", "moment_fit_wide", "fluid_step", "fluid_step_species",
             "fluid_step_closure", "maxwell_step", "vl_read_stats", "vl_reset_stats", "vl_sync_status", "vl_launch_count", "vl_fma_peak", "mlp_init", "mlp_set_weights",
             "mlp_get_weights", "mlp_set_harvest", "mlp_harvest_count", "mlp_normalize", "mlp_train", "mlp_forward",
             "mlp_grad"]
@@ -87,6 +87,7 @@ def lib():
     L.moment_fit_solve.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, _vp]
     L.moment_fit_exchange.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
     L.fluid_step.argtypes = [_vp, ctypes.c_double, _dpp, _dpp, _vp]
+    L.fluid_step_species.argtypes = [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
     L.maxwell_step.argtypes = [_vp, ctypes.c_double, _dpp, _vp]
     L.fluid_step_closure.argtypes = [_vp, ctypes.c_double, _vp]
     L.vl_read_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
@@ -322,3 +323,7 @@ def vl_fma_peak(precision, sink, stream=None):
     out = ctypes.c_double(0.0)
     _check(None, lib().vl_fma_peak(int(precision), ctypes.byref(out), ptr(sink), stream_handle(stream)))
     return out.value
+
+
+def fluid_step_species(ctx, species, dt, mom_t, mom_t1, stream=None):
+    _check(ctx, lib().fluid_step_species(ctx, species, dt, ptr(mom_t), ptr(mom_t1), stream_handle(stream)))

@@ -672,6 +672,51 @@ vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
     return VL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// One SSP-RK3 step of species s's fluid state (the body of fluid_step).
+vl_status fluid_one(vl_ctx* ctx, int s, double dt, const double* q0, const double* q1, cudaStream_t cs) {
+    const vl_desc& d = ctx->d;
+    const int ncomp = d.nvdim == 1 ? 3 : 10;
+    const int nmom = d.nvdim == 1 ? 4 : 20;
+    if (!q0 || !q1) return fail(ctx, VL_EINVAL, "moments of species %d are NULL", s);
+    double* U = ctx->fluid + (size_t)s * ncell_of(d) * ncomp;
+    vl::FluidArgs a;
+    a.U = U;
+    a.eb = ctx->eb;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.bc_y = d.bc_y;
+    a.nvdim = d.nvdim;
+    a.nmom = nmom;
+    a.precision = d.precision;
+    a.dx = d.dx;
+    a.dy = d.dy;
+    a.qm = d.q[s] / d.m[s];
+    a.dt = dt;
+    a.q0 = q0;
+    a.q1 = q1;
+    a.closure = 0;
+    a.chi_k0 = 0.0;
+    a.Usf = ctx->ws.fluid_f;
+    a.Qf = ctx->ws.fluid_f + (size_t)ncell_of(d) * 10;
+    // stage 1: U1 = U + dt L(U; Q^t)
+    a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.wq0 = 1.0; a.wq1 = 0.0; a.a0 = 0.0; a.a1 = 1.0;
+    vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+    if (e != VL_OK) return e;
+    // stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1; Q^t+1))
+    a.Us = ctx->ws.fluid_u1; a.Uout = ctx->ws.fluid_u2; a.wq0 = 0.0; a.wq1 = 1.0; a.a0 = 0.75; a.a1 = 0.25;
+    e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+    if (e != VL_OK) return e;
+    // stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2; Q^t+1/2))
+    a.Us = ctx->ws.fluid_u2; a.Uout = U; a.wq0 = 0.5; a.wq1 = 0.5; a.a0 = 1.0 / 3.0; a.a1 = 2.0 / 3.0;
+    return cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+}
+}  // namespace
+
+extern "C" {
+
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,
                      vl_stream_t stream) {
     {
@@ -679,46 +724,21 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
         if (st0 != VL_OK) return st0;
     }
     if (!mom_t || !mom_t1) return fail(ctx, VL_EINVAL, "moment arrays are NULL");
-    const vl_desc& d = ctx->d;
-    const int ncomp = d.nvdim == 1 ? 3 : 10;
-    const int nmom = d.nvdim == 1 ? 4 : 20;
-    cudaStream_t cs = (cudaStream_t)stream;
-    for (int s = 0; s < d.nspecies; ++s) {
-        if (!mom_t[s] || !mom_t1[s]) return fail(ctx, VL_EINVAL, "moments of species %d are NULL", s);
-        double* U = ctx->fluid + (size_t)s * ncell_of(d) * ncomp;
-        vl::FluidArgs a;
-        a.U = U;
-        a.eb = ctx->eb;
-        a.nx = d.nx;
-        a.ny = d.ny;
-        a.bc_y = d.bc_y;
-        a.nvdim = d.nvdim;
-        a.nmom = nmom;
-        a.precision = d.precision;
-        a.dx = d.dx;
-        a.dy = d.dy;
-        a.qm = d.q[s] / d.m[s];
-        a.dt = dt;
-        a.q0 = mom_t[s];
-        a.q1 = mom_t1[s];
-        a.closure = 0;
-        a.chi_k0 = 0.0;
-        a.Usf = ctx->ws.fluid_f;
-        a.Qf = ctx->ws.fluid_f + (size_t)ncell_of(d) * 10;
-        // stage 1: U1 = U + dt L(U; Q^t)
-        a.Us = U; a.U0 = U; a.Uout = ctx->ws.fluid_u1; a.wq0 = 1.0; a.wq1 = 0.0; a.a0 = 0.0; a.a1 = 1.0;
-        vl_status e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
-        if (e != VL_OK) return e;
-        // stage 2: U2 = 3/4 U + 1/4 (U1 + dt L(U1; Q^t+1))
-        a.Us = ctx->ws.fluid_u1; a.Uout = ctx->ws.fluid_u2; a.wq0 = 0.0; a.wq1 = 1.0; a.a0 = 0.75; a.a1 = 0.25;
-        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
-        if (e != VL_OK) return e;
-        // stage 3: U = 1/3 U + 2/3 (U2 + dt L(U2; Q^t+1/2))
-        a.Us = ctx->ws.fluid_u2; a.Uout = U; a.wq0 = 0.5; a.wq1 = 0.5; a.a0 = 1.0 / 3.0; a.a1 = 2.0 / 3.0;
-        e = cuda_check(ctx, vl::launch_fluid_stage(a, cs), "fluid_step");
+    for (int s = 0; s < ctx->d.nspecies; ++s) {
+        const vl_status e = fluid_one(ctx, s, dt, mom_t[s], mom_t1[s], (cudaStream_t)stream);
         if (e != VL_OK) return e;
     }
     return VL_OK;
+}
+
+vl_status fluid_step_species(vl_ctx* ctx, int s, double dt, const double* mom_t, const double* mom_t1,
+                             vl_stream_t stream) {
+    {
+        const vl_status st0 = check_ctx(ctx);
+        if (st0 != VL_OK) return st0;
+    }
+    if (s < 0 || s >= ctx->d.nspecies) return fail(ctx, VL_EINVAL, "species %d out of range", s);
+    return fluid_one(ctx, s, dt, mom_t, mom_t1, (cudaStream_t)stream);
 }
 
 vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_stream_t stream) {

@@ -7,10 +7,13 @@ stream, with no host synchronisation inside a step:
 2D3V (Lie splitting x, y, v):
   1. maxwell_step(dt/2)            current of the fluid state
   2. Q^t                           moments of f^t (from the previous exchange)
+  then species by species:
   3. pfc_advect_xy (x then y in one out-of-place pass; the two buffers of a
      species swap roles), pfc_advect_v(+ moments -> Q^t+1, V targets)
-  4. fluid_step(dt, Q^t, Q^t+1)    SSP-RK3, Q^t+1/2 = average
+  4. fluid_step_species(dt, Q^t, Q^t+1)  SSP-RK3, Q^t+1/2 = average, with the
+     fields frozen (a species' fluid state needs only its own moments)
   5. moment_fit                    Newton fits, exchange, limiter (+ moments of the new f)
+  and then
   6. maxwell_step(dt/2)            current of the fitted moments
 1D1V (Strang x/2, v, x/2; Poisson instead of FDTD, Sec. 3.1): E from the
 density after the first half x sweep.
@@ -142,9 +145,19 @@ class Simulation:
                     abi.pfc_advect_x(ctx, k, 1, dt, s)
                 mark("v_pass")
                 abi.pfc_advect_v(ctx, k, dt, self.mom_t1[k], s)
-                if not self.fit:
-                    last_use(k)
-        if self.fit:
+                if self.fit:
+                    # the species' own fluid step, fit and exchange before the
+                    # next species' sweeps (each fluid state needs only its own
+                    # moments and the frozen fields), so that its f is final,
+                    # and can start its way to the host, as early as possible
+                    mark("fluid")
+                    abi.fluid_step_species(ctx, k, dt, self.mom_t[k], self.mom_t1[k], s)
+                    mark("fit_solve")
+                    abi.moment_fit_solve(ctx, k, self.mom_t1[k], use_mlp, None, None, s)
+                    mark("fit_exchange")
+                    abi.moment_fit_exchange(ctx, k, self.mom_t1[k], self.mom_t[k], s)
+                last_use(k)
+        if self.fit and cfg.nvdim == 1:
             mark("fluid")
             abi.fluid_step(ctx, dt, self.mom_t, self.mom_t1, s)
             for k in range(ns):
@@ -153,7 +166,7 @@ class Simulation:
                 mark("fit_exchange")
                 abi.moment_fit_exchange(ctx, k, self.mom_t1[k], self.mom_t[k], s)
                 last_use(k)
-        else:
+        elif not self.fit:
             self.mom_t, self.mom_t1 = self.mom_t1, self.mom_t
         mark("maxwell")
         if cfg.nvdim == 1:

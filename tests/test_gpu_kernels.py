@@ -482,3 +482,31 @@ def test_empty_cells_are_left_alone(gpu, orc):
     st = abi.vl_read_stats(r.ctx)
     assert st[3] >= 1
     r.close()
+
+
+def test_fluid_step_species_equals_fluid_step(gpu, orc):
+    """fluid_step_species called species by species (in reverse order) gives
+    bit for bit the fluid state of one fluid_step call."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    torch = gpu
+    cfg = small_harris(nx=8, ny=6, nv=8, precision=32)
+    f0 = near_maxwellian_state(cfg, 720)
+    U0 = np.stack(fluid_targets(cfg, orc, f0, 721))
+    eb = W.random_fields(cfg.ncell, 722, e_scale=0.3, b_scale=0.5)
+    a = AbiRunner(cfg, f0, fluid=U0, eb=eb)
+    b = AbiRunner(cfg, f0, fluid=U0, eb=eb)
+    q0 = [a.mom() for _ in range(2)]
+    q1 = [a.mom() for _ in range(2)]
+    for k in range(2):
+        abi.moments(a.ctx, k, q0[k])
+        abi.pfc_advect_v(a.ctx, k, 0.01, q1[k])
+    abi.fluid_step(a.ctx, 0.01, q0, q1)
+    for k in (1, 0):
+        abi.fluid_step_species(b.ctx, k, 0.01, q0[k], q1[k])
+    torch.cuda.synchronize()
+    assert torch.equal(a.fluid, b.fluid)
+    with pytest.raises(abi.VlasovError):
+        abi.fluid_step_species(b.ctx, 2, 0.01, q0[0], q1[0])
+    a.close()
+    b.close()
