@@ -46,7 +46,32 @@ struct Cell {
     double k[10];   // index-space exponent of the last evaluation
     double wc[3], h[3], u0[3], sg[3];
     double tgt[10];
+    // Newton step scratch: binomial coefficients of the three axes, the
+    // transformed Gram sums, the packed Jacobian and its factor's pivots
+    double cb[3][15], U[35], W[35], J[55], dinv[10];
 };
+
+// inverse of mono4: the exponents (p, q, r) of packed monomial m
+__device__ __forceinline__ void mono4_exps(int m, int& p, int& q, int& r) {
+    p = q = r = 0;
+#pragma unroll 1
+    for (int a = 0; a <= 4; ++a)
+#pragma unroll 1
+        for (int b = 0; b <= 4 - a; ++b)
+#pragma unroll 1
+            for (int c = 0; c <= 4 - a - b; ++c)
+                if (mono4(a, b, c) == m) {
+                    p = a;
+                    q = b;
+                    r = c;
+                }
+}
+// inverse of tri: (i, j), j <= i, of packed index e
+__device__ __forceinline__ void tri_ij(int e, int& i, int& j) {
+    i = 0;
+    while (tri(i + 1, 0) <= e) ++i;
+    j = e - tri(i, 0);
+}
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
@@ -94,21 +119,60 @@ __device__ bool recurrence_ok(const double* k) {
     return __all_sync(0xffffffffu, ok);
 }
 
-// Gram sums of one line: g[p, q, r] += S_p c_y^q c_z^r
-__device__ __forceinline__ void gram_line64(double* g, const double* S, double cj, double ck) {
-    double pj[5], pk[5];
-    pj[0] = pk[0] = 1.0;
+// The block's sums are accumulated per plane: over a lane's run of lines in
+// one v_z plane the z index ck is constant, so a line's sums S_p = sum_i
+// c_i^p M are first summed with the powers of the y index cj (P: S0, S1, S2,
+// cj S0, cj S1, cj^2 S0; G[p][q] = sum S_p cj^q, p + q <= 4), and at the end
+// of the run those times the powers of ck go into the ten moments m and the
+// 35 Gram sums g.
+template <bool GRAM>
+__device__ __forceinline__ void plane_add64(double (&P)[6], double (&G)[GRAM ? 15 : 1], const double (&S)[5],
+                                            double cj) {
+    P[0] += S[0];
+    P[1] += S[1];
+    P[2] += S[2];
+    P[3] = fma(cj, S[0], P[3]);
+    P[4] = fma(cj, S[1], P[4]);
+    P[5] = fma(cj * cj, S[0], P[5]);
+    if (GRAM) {
+        double pj = 1.0;
 #pragma unroll
-    for (int q = 1; q < 5; ++q) {
-        pj[q] = pj[q - 1] * cj;
-        pk[q] = pk[q - 1] * ck;
+        for (int q = 0; q <= 4; ++q) {
+#pragma unroll
+            for (int pp = 0; pp <= 4 - q; ++pp) G[tri4(pp, q)] = fma(S[pp], pj, G[tri4(pp, q)]);
+            pj *= cj;
+        }
     }
+}
+
+template <bool GRAM>
+__device__ __forceinline__ void plane_flush64(double (&m)[10], double (&g)[GRAM ? 35 : 1], double (&P)[6],
+                                              double (&G)[GRAM ? 15 : 1], double ck) {
+    m[0] += P[0];
+    m[1] += P[1];
+    m[2] += P[3];
+    m[3] = fma(ck, P[0], m[3]);
+    m[4] += P[2];
+    m[5] += P[4];
+    m[6] = fma(ck, P[1], m[6]);
+    m[7] += P[5];
+    m[8] = fma(ck, P[3], m[8]);
+    m[9] = fma(ck * ck, P[0], m[9]);
 #pragma unroll
-    for (int p = 0; p <= 4; ++p)
+    for (int q = 0; q < 6; ++q) P[q] = 0.0;
+    if (GRAM) {
+        double pk = 1.0;
 #pragma unroll
-        for (int q = 0; q <= 4 - p; ++q)
+        for (int r = 0; r <= 4; ++r) {
 #pragma unroll
-            for (int r = 0; r <= 4 - p - q; ++r) g[mono4(p, q, r)] = fma(S[p], pj[q] * pk[r], g[mono4(p, q, r)]);
+            for (int pp = 0; pp <= 4 - r; ++pp)
+#pragma unroll
+                for (int q = 0; q <= 4 - r - pp; ++q) g[mono4(pp, q, r)] = fma(G[tri4(pp, q)], pk, g[mono4(pp, q, r)]);
+            pk *= ck;
+        }
+#pragma unroll
+        for (int q = 0; q < 15; ++q) G[q] = 0.0;
+    }
 }
 
 // Index moments (cs.m; with GRAM also the Gram sums cs.g) of M = exp(q(c))
@@ -125,9 +189,13 @@ __device__ __noinline__ bool eval64(Cell& cs) {
     double m[10];
 #pragma unroll
     for (int q = 0; q < 10; ++q) m[q] = 0.0;
-    double g[GRAM ? 35 : 1];
+    double g[GRAM ? 35 : 1], P[6], G[GRAM ? 15 : 1];
 #pragma unroll
     for (int q = 0; q < (GRAM ? 35 : 1); ++q) g[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) P[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < (GRAM ? 15 : 1); ++q) G[q] = 0.0;
     if (recurrence_ok<N>(k)) {
         const double e_in = exp(2.0 * k[4]), e_j = exp(2.0 * k[7]), e_xy = exp(k[5]);
         double Ms = 0.0, rs = 0.0, rl = 0.0;
@@ -158,17 +226,8 @@ __device__ __noinline__ bool eval64(Cell& cs) {
                 M *= r;
                 r *= e_in;
             }
-            m[0] += S[0];
-            m[1] += S[1];
-            m[2] = fma(cj, S[0], m[2]);
-            m[3] = fma(ck, S[0], m[3]);
-            m[4] += S[2];
-            m[5] = fma(cj, S[1], m[5]);
-            m[6] = fma(ck, S[1], m[6]);
-            m[7] = fma(cj * cj, S[0], m[7]);
-            m[8] = fma(cj * ck, S[0], m[8]);
-            m[9] = fma(ck * ck, S[0], m[9]);
-            if (GRAM) gram_line64(g, S, cj, ck);
+            plane_add64<GRAM>(P, G, S, cj);
+            if (j == N - 1 || l == l1 - 1) plane_flush64<GRAM>(m, g, P, G, ck);
             Ms *= rl;
             rl *= e_j;
             rs *= e_xy;
@@ -194,17 +253,8 @@ __device__ __noinline__ bool eval64(Cell& cs) {
                     S[4] = fma(M, c * c * c * c, S[4]);
                 }
             }
-            m[0] += S[0];
-            m[1] += S[1];
-            m[2] = fma(cj, S[0], m[2]);
-            m[3] = fma(ck, S[0], m[3]);
-            m[4] += S[2];
-            m[5] = fma(cj, S[1], m[5]);
-            m[6] = fma(ck, S[1], m[6]);
-            m[7] = fma(cj * cj, S[0], m[7]);
-            m[8] = fma(cj * ck, S[0], m[8]);
-            m[9] = fma(ck * ck, S[0], m[9]);
-            if (GRAM) gram_line64(g, S, cj, ck);
+            plane_add64<GRAM>(P, G, S, cj);
+            if (j == N - 1 || l == l1 - 1) plane_flush64<GRAM>(m, g, P, G, ck);
         }
     }
     bool fin = true;
@@ -257,107 +307,95 @@ __device__ __forceinline__ void w_moments64(const Cell& cs, double vol, double* 
     for (int q = 0; q < 10; ++q) D[q] *= vol;
 }
 
-// coefficients C(A, p) w^(A-p) h^p of (w + h c)^A, packed by tri(A, p)
-__device__ __forceinline__ void binom_coeffs64(double w, double h, double* c) {
-    double pw[5], ph[5];
-    pw[0] = ph[0] = 1.0;
-#pragma unroll
-    for (int e = 1; e < 5; ++e) {
-        pw[e] = pw[e - 1] * w;
-        ph[e] = ph[e - 1] * h;
-    }
-#pragma unroll
-    for (int A = 0; A <= 4; ++A)
-#pragma unroll
-        for (int p = 0; p <= A; ++p) c[tri(A, p)] = (double)binom4(A, p) * pw[A - p] * ph[p];
-}
-
-// Newton direction: the Gram matrix in w-space from the index sums (three
-// separable binomial transforms), Cholesky, J step = -G. Lane 0; returns
-// (to every lane) whether J was positive definite.
+// Newton direction, with the warp's lanes sharing the work (an FP64 warp
+// instruction costs the FP64 pipe the same with one lane active as with
+// 32): the binomial coefficients of (w + h c)^A per axis, the Gram matrix
+// in w-space from the index sums by three separable transforms (one
+// output per lane), an LDL^T factorisation whose column updates run one
+// entry per lane, and the two triangular solves with one unknown per lane.
+// Returns (to every lane) whether J was positive definite.
 __device__ __noinline__ bool newton_step64(Cell& cs, const double* G, double vol) {
-    int ok = 1;
-    if (lane_id() == 0) {
-        double cx[15], cy[15], cz[15], U[35], W[35];
-        binom_coeffs64(cs.wc[0], cs.h[0], cx);
-        binom_coeffs64(cs.wc[1], cs.h[1], cy);
-        binom_coeffs64(cs.wc[2], cs.h[2], cz);
-        const double* g = cs.g;
+    const int lane = lane_id();
+    if (lane < 15) {
+        int A, pp;
+        tri_ij(lane, A, pp);
+        const double bn = (double)binom4(A, pp);
 #pragma unroll
-        for (int A = 0; A <= 4; ++A)
-#pragma unroll
-            for (int q = 0; q <= 4 - A; ++q)
-#pragma unroll
-                for (int r = 0; r <= 4 - A - q; ++r) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int p = 0; p <= A; ++p) s = fma(cx[tri(A, p)], g[mono4(p, q, r)], s);
-                    U[mono4(A, q, r)] = s;
-                }
-#pragma unroll
-        for (int A = 0; A <= 4; ++A)
-#pragma unroll
-            for (int B = 0; B <= 4 - A; ++B)
-#pragma unroll
-                for (int r = 0; r <= 4 - A - B; ++r) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int q = 0; q <= B; ++q) s = fma(cy[tri(B, q)], U[mono4(A, q, r)], s);
-                    W[mono4(A, B, r)] = s;
-                }
-#pragma unroll
-        for (int A = 0; A <= 4; ++A)
-#pragma unroll
-            for (int B = 0; B <= 4 - A; ++B)
-#pragma unroll
-                for (int C = 0; C <= 4 - A - B; ++C) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int r = 0; r <= C; ++r) s = fma(cz[tri(C, r)], W[mono4(A, B, r)], s);
-                    U[mono4(A, B, C)] = s * vol;
-                }
-        double J[55], inv[10];
-#pragma unroll
-        for (int a = 0; a < 10; ++a)
-#pragma unroll
-            for (int b = 0; b <= a; ++b)
-                J[tri(a, b)] = U[mono4(expo(a, 0) + expo(b, 0), expo(a, 1) + expo(b, 1), expo(a, 2) + expo(b, 2))];
-#pragma unroll
-        for (int i = 0; i < 10; ++i)
-#pragma unroll
-            for (int j = 0; j <= i; ++j) {
-                double s = J[tri(i, j)];
-#pragma unroll
-                for (int q = 0; q < j; ++q) s = fma(-J[tri(i, q)], J[tri(j, q)], s);
-                if (i == j) {
-                    ok &= s > 0.0 ? 1 : 0;
-                    const double d = sqrt(fmax(s, 1e-300));
-                    J[tri(i, i)] = d;
-                    inv[i] = 1.0 / d;
-                } else {
-                    J[tri(i, j)] = s * inv[j];
-                }
-            }
-        double y[10];
-#pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            double s = -G[i];
-#pragma unroll
-            for (int q = 0; q < i; ++q) s = fma(-J[tri(i, q)], y[q], s);
-            y[i] = s * inv[i];
+        for (int ax = 0; ax < 3; ++ax) {
+            double v = bn;
+            for (int e = 0; e < A - pp; ++e) v *= cs.wc[ax];
+            for (int e = 0; e < pp; ++e) v *= cs.h[ax];
+            cs.cb[ax][lane] = v;
         }
-#pragma unroll
-        for (int i = 9; i >= 0; --i) {
-            double s = y[i];
-#pragma unroll
-            for (int q = i + 1; q < 10; ++q) s = fma(-J[tri(q, i)], y[q], s);
-            y[i] = s * inv[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 10; ++i) cs.step[i] = y[i];
     }
     __syncwarp();
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    // x: U[A, q, r] = sum_p c_x[A][p] g[p, q, r]
+    for (int m = lane; m < 35; m += 32) {
+        int A, q, r;
+        mono4_exps(m, A, q, r);
+        double acc = 0.0;
+        for (int pp = 0; pp <= A; ++pp) acc = fma(cs.cb[0][tri(A, pp)], cs.g[mono4(pp, q, r)], acc);
+        cs.U[m] = acc;
+    }
+    __syncwarp();
+    // y: W[A, B, r] = sum_q c_y[B][q] U[A, q, r]
+    for (int m = lane; m < 35; m += 32) {
+        int A, B, r;
+        mono4_exps(m, A, B, r);
+        double acc = 0.0;
+        for (int q = 0; q <= B; ++q) acc = fma(cs.cb[1][tri(B, q)], cs.U[mono4(A, q, r)], acc);
+        cs.W[m] = acc;
+    }
+    __syncwarp();
+    // z: U[A, B, C] = vol sum_r c_z[C][r] W[A, B, r]
+    for (int m = lane; m < 35; m += 32) {
+        int A, B, C;
+        mono4_exps(m, A, B, C);
+        double acc = 0.0;
+        for (int r = 0; r <= C; ++r) acc = fma(cs.cb[2][tri(C, r)], cs.W[mono4(A, B, r)], acc);
+        cs.U[m] = acc * vol;
+    }
+    __syncwarp();
+    for (int e = lane; e < 55; e += 32) {
+        int ia, ib;
+        tri_ij(e, ia, ib);
+        cs.J[e] = cs.U[mono4(expo(ia, 0) + expo(ib, 0), expo(ia, 1) + expo(ib, 1), expo(ia, 2) + expo(ib, 2))];
+    }
+    __syncwarp();
+    // LDL^T, right-looking: column j's pivot d_j, multipliers l_ij = a_ij / d_j
+    // (stored in place), then the trailing update a_ik -= l_ij d_j l_kj
+    bool ok = true;
+    for (int j = 0; j < 10; ++j) {
+        const double d = cs.J[tri(j, j)];
+        ok = ok && d > 0.0;
+        const double di = 1.0 / fmax(d, 1e-300);
+        double lij = 0.0;
+        if (lane > j && lane < 10) lij = cs.J[tri(lane, j)] * di;
+        __syncwarp();
+        for (int e = lane; e < 55; e += 32) {
+            int i, k;
+            tri_ij(e, i, k);
+            if (k > j) cs.J[e] -= cs.J[tri(i, j)] * cs.J[tri(k, j)] * di;
+        }
+        __syncwarp();
+        if (lane > j && lane < 10) cs.J[tri(lane, j)] = lij;
+        if (lane == 0) cs.dinv[j] = di;
+        __syncwarp();
+    }
+    // L y = -G (unit diagonal), D z = y, L^T x = z; unknown i on lane i
+    double b = lane < 10 ? -G[lane] : 0.0;
+    for (int i = 0; i < 10; ++i) {
+        const double yi = __shfl_sync(0xffffffffu, b, i);
+        if (lane > i && lane < 10) b = fma(-cs.J[tri(lane, i)], yi, b);
+    }
+    if (lane < 10) b *= cs.dinv[lane];
+    for (int i = 9; i >= 0; --i) {
+        const double xi = __shfl_sync(0xffffffffu, b, i);
+        if (lane < i) b = fma(-cs.J[tri(i, lane)], xi, b);
+    }
+    if (lane < 10) cs.step[lane] = b;
+    __syncwarp();
+    return __all_sync(0xffffffffu, ok);
 }
 
 // Fit set-up (lane 0, targets in cs.tgt): scaled coordinates, w-space
