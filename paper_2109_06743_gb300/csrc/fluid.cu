@@ -150,13 +150,17 @@ template <typename R>
 __device__ __forceinline__ void closure_e3(const R* s, R* e3) {
     const R n = s[0];
     if (!(n > R(0))) {
+#pragma unroll
         for (int k = 0; k < 10; ++k) e3[k] = R(0);
         return;
     }
     const R inv = R(1) / n;
     const R v[3] = {s[1] * inv, s[2] * inv, s[3] * inv};
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
         for (int b = a; b < 3; ++b)
+#pragma unroll
             for (int k = b; k < 3; ++k)
                 e3[s3(a, b, k)] = v[k] * s[4 + s2(a, b)] + v[a] * s[4 + s2(k, b)] + v[b] * s[4 + s2(k, a)] -
                                   R(2) * n * v[k] * v[a] * v[b];
@@ -166,10 +170,13 @@ __device__ __forceinline__ void closure_e3(const R* s, R* e3) {
 template <typename R>
 __device__ __forceinline__ void theta_cell(const FluidCtx& c, int ix, int iy, R* th) {
     R s[10];
+#pragma unroll
     for (int k = 0; k < 10; ++k) s[k] = state_at<R>(c, k, ix, iy);
     const R n = s[0];
     const R inv = n > R(0) ? R(1) / n : R(0);
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
         for (int b = a; b < 3; ++b) th[s2(a, b)] = s[4 + s2(a, b)] * inv - (s[1 + a] * inv) * (s[1 + b] * inv);
 }
 
@@ -190,16 +197,90 @@ __device__ __forceinline__ R value_at(const FluidCtx& c, bool q, int k, long lon
 // cells of the stencil are resolved once; each of the three middle cells is
 // reconstructed once (its left and right interface values), which serves
 // both interfaces.
-template <typename R>
-__device__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R* Hp) {
+// The numerical fluxes of cell_fluxes with the third moments from f (no
+// closure), one flux component at a time so that few values are live: the
+// interface states of component k (for the dissipation term) and of the
+// component whose value is k's flux (state component 1+dir, 4+(dir,k-1) or
+// third moment (dir,a,b)). The wave speeds come from the cell averages.
+template <typename R, int NV>
+__device__ __forceinline__ void cell_fluxes_lean(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R* Hp) {
+    constexpr int NC = NV == 1 ? 3 : 10;
     long long id[5];
     bool mir[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o)
+        id[o] = resolve(*c.a, ix + (dir == 0 ? o - 2 : 0), iy + (dir == 1 ? o - 2 : 0), &mir[o]);
+    // wave speeds |u_d| + sqrt(3 Theta_dd) of cells -1, 0, +1
+    R ws[3];
+    const int kd = NV == 1 ? 2 : 4 + s2(dir, dir);
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const R n = value_at<R>(c, false, 0, id[o + 1], mir[o + 1]);
+        const R nu = value_at<R>(c, false, 1 + dir, id[o + 1], mir[o + 1]);
+        const R e2 = value_at<R>(c, false, kd, id[o + 1], mir[o + 1]);
+        R w = R(0);
+        if (n > R(0)) {
+            const R ud = nu / n;
+            R th = e2 / n - ud * ud;
+            if (th < R(0)) th = R(0);
+            w = fabs(ud) + sqrt(R(3) * th);
+        }
+        ws[o] = w;
+    }
+    const R sm = fmax(ws[0], ws[1]), sp = fmax(ws[1], ws[2]);
+    // interface states of one component: the right value of cell -1, the
+    // left and right values of cell 0 and the left value of cell +1
+    auto recon = [&](bool q, int k, R& rm, R& l0, R& r0, R& lp) {
+        const R a0 = value_at<R>(c, q, k, id[0], mir[0]), a1 = value_at<R>(c, q, k, id[1], mir[1]);
+        const R a2 = value_at<R>(c, q, k, id[2], mir[2]), a3 = value_at<R>(c, q, k, id[3], mir[3]);
+        const R a4 = value_at<R>(c, q, k, id[4], mir[4]);
+        R l, r;
+        cweno3_point<R>(a0, a1, a2, &l, &r);
+        rm = r;
+        cweno3_point<R>(a1, a2, a3, &l0, &r0);
+        cweno3_point<R>(a2, a3, a4, &lp, &r);
+    };
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        R um, u0, up, cp;
+        recon(false, k, um, u0, up, cp);
+        // the flux of component k
+        bool fq;
+        int fk;
+        if (NV == 1) {
+            fq = k == 2;
+            fk = k == 0 ? 1 : (k == 1 ? 2 : 0);
+        } else if (k == 0) {
+            fq = false;
+            fk = 1 + dir;
+        } else if (k < 4) {
+            fq = false;
+            fk = 4 + s2(dir, k - 1);
+        } else {
+            const int ab[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+            fq = true;
+            fk = s3(dir, ab[k - 4][0], ab[k - 4][1]);
+        }
+        R fm, f0, fp, fc;
+        recon(fq, fk, fm, f0, fp, fc);
+        Hm[k] = R(0.5) * (fm + f0) - R(0.5) * sm * (u0 - um);
+        Hp[k] = R(0.5) * (fp + fc) - R(0.5) * sp * (cp - up);
+    }
+}
+
+template <typename R, int NV>
+__device__ __forceinline__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R* Hp) {
+    constexpr int NC = NV == 1 ? 3 : 10, NQ = NV == 1 ? 1 : 10;
+    long long id[5];
+    bool mir[5];
+#pragma unroll
     for (int o = 0; o < 5; ++o)
         id[o] = resolve(*c.a, ix + (dir == 0 ? o - 2 : 0), iy + (dir == 1 ? o - 2 : 0), &mir[o]);
     // uE[p][side]: reconstruction in cell p-1 (p = 0, 1, 2 for cells -1, 0, +1)
     R um[10], u0[10], up[10], cm[10], c0[10], cp[10];  // left/right states of the two interfaces
     R qm_[10], q0_[10], qp_[10], qmm[10];
-    for (int k = 0; k < c.nc; ++k) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
         const R a0 = value_at<R>(c, false, k, id[0], mir[0]), a1 = value_at<R>(c, false, k, id[1], mir[1]);
         const R a2 = value_at<R>(c, false, k, id[2], mir[2]), a3 = value_at<R>(c, false, k, id[3], mir[3]);
         const R a4 = value_at<R>(c, false, k, id[4], mir[4]);
@@ -224,7 +305,8 @@ __device__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R
     if (c.a->closure) {
         closure_e3<R>(cp, qcp);
     } else {
-        for (int k = 0; k < c.nq; ++k) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
             const R a0 = value_at<R>(c, true, k, id[0], mir[0]), a1 = value_at<R>(c, true, k, id[1], mir[1]);
             const R a2 = value_at<R>(c, true, k, id[2], mir[2]), a3 = value_at<R>(c, true, k, id[3], mir[3]);
             const R a4 = value_at<R>(c, true, k, id[4], mir[4]);
@@ -238,10 +320,11 @@ __device__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R
             qcp[k] = l;
         }
     }
-    const int nvdim = c.a->nvdim;
+    constexpr int nvdim = NV;
     const R sm = fmax(wave_speed<R>(nvdim, dir, cm), wave_speed<R>(nvdim, dir, c0));
     const R sp = fmax(wave_speed<R>(nvdim, dir, c0), wave_speed<R>(nvdim, dir, qmm));
-    for (int k = 0; k < c.nc; ++k) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
         Hm[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, um, qm_) + flux_of<R>(nvdim, dir, k, u0, q0_)) -
                 R(0.5) * sm * (u0[k] - um[k]);
         Hp[k] = R(0.5) * (flux_of<R>(nvdim, dir, k, up, qp_) + flux_of<R>(nvdim, dir, k, cp, qcp)) -
@@ -249,34 +332,51 @@ __device__ void cell_fluxes(const FluidCtx& c, int dir, int ix, int iy, R* Hm, R
     }
 }
 
-template <typename R>
-__global__ void fluid_stage_kernel(FluidArgs a) {
+// One thread per cell and stage; NV = 1 (1D1V: three components) or 3
+// (2D3V: ten), a compile-time count so that the per-component arrays stay in
+// registers.
+#ifndef VL_FLUID_MIN_BLOCKS_F32
+#define VL_FLUID_MIN_BLOCKS_F32 8
+#endif
+#ifndef VL_FLUID_MIN_BLOCKS_F64
+#define VL_FLUID_MIN_BLOCKS_F64 1
+#endif
+template <typename R, int NV, bool CLOSURE>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? VL_FLUID_MIN_BLOCKS_F32 : VL_FLUID_MIN_BLOCKS_F64)
+    fluid_stage_kernel(FluidArgs a) {
+    constexpr int NC = NV == 1 ? 3 : 10;
     long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (cell >= (long long)a.nx * a.ny) return;
     const int ix = (int)(cell % a.nx), iy = (int)(cell / a.nx);
     FluidCtx c;
     c.a = &a;
-    c.nc = a.nvdim == 1 ? 3 : 10;
-    c.nq = a.nvdim == 1 ? 1 : 10;
-    c.qoff = a.nvdim == 1 ? 3 : 10;
+    c.nc = NC;
+    c.nq = NV == 1 ? 1 : 10;
+    c.qoff = NV == 1 ? 3 : 10;
     c.use0 = a.wq0 != 0.0;
     c.use1 = a.wq1 != 0.0;
     R L[10];
-    for (int k = 0; k < c.nc; ++k) L[k] = R(0);
-    const int ndir = a.nvdim == 1 ? 1 : 2;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) L[k] = R(0);
+    constexpr int ndir = NV == 1 ? 1 : 2;
     R Hm[10], Hp[10];
+#pragma unroll
     for (int dir = 0; dir < ndir; ++dir) {
         const R invh = (R)(1.0 / (dir == 0 ? a.dx : a.dy));
-        cell_fluxes<R>(c, dir, ix, iy, Hm, Hp);
+        if (CLOSURE) cell_fluxes<R, NV>(c, dir, ix, iy, Hm, Hp);
+        else cell_fluxes_lean<R, NV>(c, dir, ix, iy, Hm, Hp);
         // walls: the interface beyond the last row is the wall itself
         // (mirror ghosts already give its flux); nothing special needed
-        for (int k = 0; k < c.nc; ++k) L[k] -= (Hp[k] - Hm[k]) * invh;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) L[k] -= (Hp[k] - Hm[k]) * invh;
     }
     R u[10], eb[6];
-    for (int k = 0; k < c.nc; ++k) u[k] = (R)a.Us[cell * c.nc + k];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) u[k] = (R)a.Us[cell * NC + k];
+#pragma unroll
     for (int k = 0; k < 6; ++k) eb[k] = (R)a.eb[cell * 6 + k];
     const R qm = (R)a.qm;
-    if (a.nvdim == 1) {
+    if (NV == 1) {
         L[1] += qm * u[0] * eb[0];
         L[2] += qm * R(2) * u[1] * eb[0];
     } else {
@@ -287,17 +387,22 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
         L[2] += qm * (u[0] * E[1] + nu[2] * B[0] - nu[0] * B[2]);
         L[3] += qm * (u[0] * E[2] + nu[0] * B[1] - nu[1] * B[0]);
         R M[3][3];
+#pragma unroll
         for (int p = 0; p < 3; ++p)
+#pragma unroll
             for (int q = 0; q < 3; ++q) M[p][q] = u[4 + s2(p, q)];
         R C[3][3];
+#pragma unroll
         for (int p = 0; p < 3; ++p) {
             C[p][0] = M[p][1] * B[2] - M[p][2] * B[1];
             C[p][1] = M[p][2] * B[0] - M[p][0] * B[2];
             C[p][2] = M[p][0] * B[1] - M[p][1] * B[0];
         }
+#pragma unroll
         for (int p = 0; p < 3; ++p)
+#pragma unroll
             for (int q = p; q < 3; ++q) L[4 + s2(p, q)] += qm * (nu[p] * E[q] + nu[q] * E[p] + C[p][q] + C[q][p]);
-        if (a.closure) {
+        if (CLOSURE) {
             // heat flux of the closure: -(1/m) div Q = chi_k0 n v_t lap theta,
             // v_t = sqrt(tr(theta) / 3), five-point Laplacian
             R t0[6], tw[6], te[6], ts[6], tn[6];
@@ -310,14 +415,16 @@ __global__ void fluid_stage_kernel(FluidArgs a) {
             const R vt = sqrt(tr > R(0) ? tr / R(3) : R(0));
             const R coef = (R)a.chi_k0 * u[0] * vt;
             const R ix2 = (R)(1.0 / (a.dx * a.dx)), iy2 = (R)(1.0 / (a.dy * a.dy));
+#pragma unroll
             for (int k = 0; k < 6; ++k)
                 L[4 + k] += coef * ((te[k] - R(2) * t0[k] + tw[k]) * ix2 + (tn[k] - R(2) * t0[k] + ts[k]) * iy2);
         }
     }
-    for (int k = 0; k < c.nc; ++k) {
-        double us = a.Us[cell * c.nc + k];
-        double u0 = a.a0 != 0.0 ? a.U0[cell * c.nc + k] : 0.0;
-        a.Uout[cell * c.nc + k] = a.a0 * u0 + a.a1 * (us + a.dt * (double)L[k]);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        double us = a.Us[cell * NC + k];
+        double u0 = a.a0 != 0.0 ? a.U0[cell * NC + k] : 0.0;
+        a.Uout[cell * NC + k] = a.a0 * u0 + a.a1 * (us + a.dt * (double)L[k]);
     }
 }
 
@@ -349,8 +456,17 @@ cudaError_t launch_fluid_stage(const FluidArgs& args, cudaStream_t st) {
         fluid_prep_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
         count_launch();
     }
-    if (a.precision == 64) fluid_stage_kernel<double><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
-    else fluid_stage_kernel<float><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+    const unsigned grid = (unsigned)((n + threads - 1) / threads);
+    if (a.nvdim == 1) {
+        if (a.precision == 64) fluid_stage_kernel<double, 1, false><<<grid, threads, 0, st>>>(a);
+        else fluid_stage_kernel<float, 1, false><<<grid, threads, 0, st>>>(a);
+    } else if (a.closure) {
+        if (a.precision == 64) fluid_stage_kernel<double, 3, true><<<grid, threads, 0, st>>>(a);
+        else fluid_stage_kernel<float, 3, true><<<grid, threads, 0, st>>>(a);
+    } else {
+        if (a.precision == 64) fluid_stage_kernel<double, 3, false><<<grid, threads, 0, st>>>(a);
+        else fluid_stage_kernel<float, 3, false><<<grid, threads, 0, st>>>(a);
+    }
     count_launch();
     return cudaGetLastError();
 }
