@@ -40,7 +40,8 @@ __device__ __forceinline__ void line_products_z(T (&m)[20], T S0, T S1, T S2, T 
 }
 
 // reduce the per-thread products over the CTA and write the 20 physical
-// raw moments to out (uses red[20 * 32 + 20]; contains a __syncthreads).
+// raw moments to out (uses red[20 * MAXW + 20] for at most MAXW warps;
+// contains a __syncthreads).
 // Warp partial sums are combined in T by lanes 0..19 of warp 0; only the
 // final binomial expansion runs in FP64 (on GB300 an FP64 warp instruction
 // occupies the pipe for many cycles however few lanes are active, so FP64
@@ -58,7 +59,7 @@ __device__ __forceinline__ T rs_step(T keep_lo, T keep_hi, bool hi, int o) {
     return (hi ? keep_hi : keep_lo) + __shfl_xor_sync(0xffffffffu, send, o);
 }
 
-template <typename T>
+template <typename T, int MAXW = 32>
 __device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* out, const MomConv& conv) {
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31, nwarp = blockDim.x >> 5;
@@ -79,7 +80,7 @@ __device__ __forceinline__ void reduce_moments(T (&m)[20], double* red, double* 
     T* part = reinterpret_cast<T*>(red);
     if (valid) part[warp * 20 + idx] = e;
     __syncthreads();
-    double* im = red + 20 * 32;
+    double* im = red + 20 * MAXW;
     if (t < 20) {
         T sacc = T(0);
         for (int w = 0; w < nwarp; ++w) sacc += part[w * 20 + t];

@@ -14,7 +14,12 @@
 //
 // Shared-memory layout of a block: element (i, j, k) (i = v_x index fastest)
 // at (k N + j)(N + 1) + i: x lines are padded to N+1 so that a warp walking
-// 32 different lines hits distinct banks.
+// 32 different lines hits distinct banks (32 consecutive v_z lines at fixed
+// v_z index span 33 words: one bank is hit twice).
+//
+// FP32 blocks run velocity_pair_kernel (two lines per thread, packed FP32x2
+// arithmetic, every line walked upwards); FP64 blocks run velocity_kernel
+// (one line per thread, walked in the direction of its displacement).
 #include "common.cuh"
 #include "kernels.cuh"
 #include "block_moments.cuh"
@@ -297,9 +302,9 @@ constexpr int vel_threads(int n) { return ((n * n + 31) / 32) * 32; }
 
 // Block copies with the CTA's compile-time thread count, so the loops unroll
 // and (for N^2 a multiple of 32) every index step is a constant.
-template <typename T, int N>
+template <typename T, int N, int NTH = vel_threads(N)>
 __device__ __forceinline__ void load_block(T* blk, const T* src) {
-    constexpr int V = N * N * N, NTH = vel_threads(N);
+    constexpr int V = N * N * N;
 #pragma unroll 4
     for (int e = threadIdx.x; e < V; e += NTH) {
         int i = e % N, jk = e / N;
@@ -309,9 +314,9 @@ __device__ __forceinline__ void load_block(T* blk, const T* src) {
 
 // asynchronous element copies of one block into the padded layout (the
 // padding breaks 16-byte alignment of the rows, so element-sized copies)
-template <typename T, int N>
+template <typename T, int N, int NTH = vel_threads(N)>
 __device__ __forceinline__ void prefetch_block(T* blk, const T* src) {
-    constexpr int V = N * N * N, NTH = vel_threads(N);
+    constexpr int V = N * N * N;
 #pragma unroll 4
     for (int e = threadIdx.x; e < V; e += NTH) {
         const int i = e % N, jk = e / N;
@@ -321,12 +326,47 @@ __device__ __forceinline__ void prefetch_block(T* blk, const T* src) {
     }
 }
 
+// The same copies when the thread count is a multiple of the row length and
+// the block a multiple of the thread count: every thread keeps one column of
+// rows, so both addresses step by compile-time constants (no per-element
+// index arithmetic).
+template <int N, int NTH>
+constexpr bool rows_tile() { return NTH % N == 0 && (N * N * N) % NTH == 0; }
+template <int N, int NTH>
+constexpr bool groups_tile() { return (4 * NTH) % N == 0 && (N * N * N / 4) % NTH == 0; }
+
+template <int N, int NTH>
+__device__ __forceinline__ void prefetch_block_rows(float* blk, const float* src) {
+    constexpr int R = NTH / N, U = N * N * N / NTH;
+    const int t = threadIdx.x;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(blk + (t / N) * (N + 1) + t % N);
+    const float* g = src + t;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d + 4u * (unsigned)(u * R * (N + 1))),
+                     "l"(g + u * NTH)
+                     : "memory");
+}
+
+template <int N, int NTH>
+__device__ __forceinline__ void store_block_groups(float* dst, const float* blk) {
+    constexpr int U = N * N * N / 4 / NTH, R = 4 * NTH / N;
+    const int t = threadIdx.x;
+    const float* row = blk + (4 * t / N) * (N + 1) + (4 * t) % N;
+    float* g = dst + 4 * t;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float* q = row + u * R * (N + 1);
+        *reinterpret_cast<float4*>(g + u * 4 * NTH) = make_float4(q[0], q[1], q[2], q[3]);
+    }
+}
+
 // write the block back; with vec (16-byte aligned f) in 16-byte stores: a
 // row holds N values (N a multiple of 4), so each group of 16 bytes comes
 // from one padded row
-template <typename T, int N>
+template <typename T, int N, int NTH = vel_threads(N)>
 __device__ __forceinline__ void store_block(T* dst, const T* blk, bool vec) {
-    constexpr int V = N * N * N, NTH = vel_threads(N);
+    constexpr int V = N * N * N;
     constexpr int per = 16 / (int)sizeof(T);
     static_assert(N % 4 == 0, "rows of whole 16-byte groups");
     if (!vec) {
@@ -352,10 +392,10 @@ __device__ __forceinline__ void store_block(T* dst, const T* blk, bool vec) {
     }
 }
 
-// One CTA per velocity block at a time (persistent over cells). With
-// a.nbuf == 2 the next cell's block is copied in while the current one is
-// advected. Registers are capped at 64 per thread (FP32) or 128 (FP64)
-// where the block size allows, so that several CTAs share an SM.
+// One CTA per velocity block at a time (persistent over cells); the FP64
+// pass. With a.nbuf == 2 the next cell's block is copied in while the
+// current one is advected. Registers are capped at 128 per thread where the
+// block size allows, so that several CTAs share an SM.
 constexpr int vel_min_blocks(int n, int es) {
     return 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) > 0 ? 65536 / ((es == 8 ? 128 : 64) * vel_threads(n)) : 1;
 }
@@ -398,6 +438,315 @@ __global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) 
         }
         if (a.mom_out) block_moments<T, N>(blk, red, a.mom_out + cell * 20, a.conv);
         store_block<T, N>(f + cell * V, blk, a.vec != 0);
+        __syncthreads();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ------------------------------------------------ FP32: two lines per thread
+//
+// The FP32 pass pairs the lines of every sweep two to a thread and updates
+// both with packed FP32x2 arithmetic (add/sub/mul/fma.f32x2), which halves
+// the issue slots of the line update; the limiter's min/max stay scalar.
+//
+// Every line is walked in increasing index order whatever the sign of its
+// displacement, so that each shared-memory access is a compile-time offset
+// from the line's start. With a_i = f_{i+1} - f_i (zero ghosts outside the
+// box), U_i = min(a_i, 2 f_i) and D_i = max(a_{i-1}, -2 f_i), the flux that
+// leaves cell i in the direction of the displacement is
+//   c >= 0: alpha (f_i + A U_i + B D_i), out through face i + 1/2,
+//   c <  0: alpha (f_i - A D_i - B U_i), out through face i - 1/2,
+// (A = (1 - alpha)(2 - alpha)/6, B = (1 - alpha)(1 + alpha)/6; the second
+// is the first one mirrored). With phi_i = a0 f_i + P U_i + Q D_i the flux
+// through face i + 1/2 counted in the +v direction (a0, P, Q = alpha,
+// alpha A, alpha B for c >= 0; -alpha, alpha B, alpha A for c < 0), the new
+// value of cell q is f_q + c0 phi_q + cm phi_{q-1} + cp phi_{q+1}, with
+// (c0, cm, cp) = (-1, 1, 0) or (1, 0, -1). At the box faces nothing flows
+// out: the first cell drops its own term for c < 0 (coefficient -cm), the
+// last one for c >= 0 (coefficient -cp).
+
+namespace pair {
+
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) {
+    unsigned long long ua, ub, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(ua), "l"(ub));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+constexpr int threads(int n) { return ((n * n / 2 + 31) / 32) * 32; }
+constexpr int warps(int n) { return threads(n) / 32; }
+// CTAs per SM the register cap is sized for
+constexpr int min_blocks(int n) { return n <= 8 ? 16 : (n <= 12 ? 6 : (n <= 16 ? 5 : 2)); }
+
+// physical exponents (x, y, z) of moment o, packed x + 4 y + 16 z
+__host__ __device__ constexpr int mono_exp(int o) {
+    constexpr int e[20] = {0, 1, 4, 16, 2, 5, 17, 8, 20, 32, 3, 6, 18, 9, 21, 33, 12, 24, 36, 48};
+    return e[o];
+}
+
+// both lines' coefficients at once, in packed arithmetic: with sg = +-1 the
+// sign of the displacement, h = (1 - alpha)/6 and t = sg (1/2 - alpha),
+// alpha A and alpha B are alpha h (3/2 + t) and alpha h (3/2 - t) in the
+// order (P, Q) of the formula above
+struct PairCoef {
+    float2 a0, P, Q, c0, cm, cp;
+    int s1, s2;
+    bool f1, f2;
+};
+
+template <int N>
+__device__ __forceinline__ PairCoef pair_coef(float2 c) {
+    PairCoef k;
+    k.f1 = c.x >= 0.0f;
+    k.f2 = c.y >= 0.0f;
+    const float2 sg = make_float2(k.f1 ? 1.0f : -1.0f, k.f2 ? 1.0f : -1.0f);
+    // clamped at N cells (fminf also maps NaN to N)
+    const float2 ca = make_float2(fminf(fabsf(c.x), float(N)), fminf(fabsf(c.y), float(N)));
+    const float2 fl = make_float2(floorf(ca.x), floorf(ca.y));
+    k.s1 = (int)fl.x;
+    k.s2 = (int)fl.y;
+    const float2 al = sub(ca, fl);
+    const float2 sixth = make_float2(1.0f / 6.0f, 1.0f / 6.0f), half = make_float2(0.5f, 0.5f);
+    const float2 h = fma(neg(al), sixth, sixth);
+    const float2 t = mul(sg, sub(half, al));
+    const float2 ah = mul(al, h);
+    const float2 th = make_float2(1.5f, 1.5f);
+    k.P = mul(ah, add(th, t));
+    k.Q = mul(ah, sub(th, t));
+    k.a0 = mul(sg, al);
+    k.c0 = neg(sg);
+    k.cm = fma(sg, half, half);
+    k.cp = sub(k.cm, make_float2(1.0f, 1.0f));
+    return k;
+}
+
+// integer part of the displacement of one line: g (the fractional update,
+// both box faces closed) moves s cells in the direction of the displacement,
+// what would leave the box piles up in the last cell, the cells it leaves
+// become zero (the one-dimensional sweep at any displacement, Sec. 2.1)
+template <int N, int ST, int C>
+__device__ __forceinline__ void shift_store(float* line, const float2 (&g)[N], int s, bool fwd) {
+    auto at = [&](int q) -> float { return C == 0 ? g[q].x : g[q].y; };
+    if (s == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) line[q * ST] = at(q);
+        return;
+    }
+    float acc = 0.0f;
+    if (fwd) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (q + s < N - 1) line[(q + s) * ST] = at(q);
+            else acc += at(q);
+        }
+        line[(N - 1) * ST] = acc;
+#pragma unroll
+        for (int p = 0; p < N - 1; ++p)
+            if (p < s) line[p * ST] = 0.0f;
+    } else {
+#pragma unroll
+        for (int q = N - 1; q >= 0; --q) {
+            if (q - s > 0) line[(q - s) * ST] = at(q);
+            else acc += at(q);
+        }
+        line[0] = acc;
+#pragma unroll
+        for (int p = 1; p < N; ++p)
+            if (p > N - 1 - s) line[p * ST] = 0.0f;
+    }
+}
+
+// the 20 raw-moment products of one line along axis AX with centred sums
+// S[0..3] at centred indices e (lower other axis), z (higher other axis)
+template <int AX>
+__device__ __forceinline__ void line_moments(float (&m)[20], const float (&S)[4], float e, float z) {
+    constexpr int alo = AX == 0 ? 1 : 0, ahi = AX == 2 ? 1 : 2;
+    const float pe[4] = {1.0f, e, e * e, e * e * e};
+    const float pz[4] = {1.0f, z, z * z, z * z * z};
+#pragma unroll
+    for (int o = 0; o < 20; ++o) {
+        const int x = mono_exp(o);
+        const int ex[3] = {x & 3, (x >> 2) & 3, (x >> 4) & 3};
+        const int a = ex[AX], b = ex[alo], c = ex[ahi];
+        if (b == 0 && c == 0) m[o] += S[a];
+        else if (c == 0) m[o] = fmaf(S[a], pe[b], m[o]);
+        else if (b == 0) m[o] = fmaf(S[a], pz[c], m[o]);
+        else m[o] = fmaf(S[a], pe[b] * pz[c], m[o]);
+    }
+}
+
+// One sweep along velocity axis AX over the pair of lines (lo1, hi1),
+// (lo2, hi2) of this thread. RAGGED: some threads hold fewer than two lines
+// (v1, v2 false), their loads give zero and their stores are skipped. MOM:
+// this is the block's last sweep: the 20 moment products of the result are
+// formed from the registers and reduced over the CTA into out.
+template <int N, int AX, bool RAGGED, bool MOM>
+__device__ __forceinline__ void sweep(float* blk, const float* sh, const float* vc, const float* inv_dv, int lo1,
+                                      int hi1, int lo2, int hi2, bool v1, bool v2, double* red, double* out,
+                                      const MomConv& conv) {
+    constexpr int ST = AX == 0 ? 1 : (AX == 1 ? N + 1 : N * (N + 1));
+    constexpr int alo = AX == 0 ? 1 : 0, ahi = AX == 2 ? 1 : 2;
+    auto start = [](int lo, int hi) {
+        return AX == 0 ? padded<N>(0, lo, hi) : (AX == 1 ? padded<N>(lo, 0, hi) : padded<N>(lo, hi, 0));
+    };
+    float* const L1 = blk + start(lo1, hi1);
+    float* const L2 = blk + start(lo2, hi2);
+    const float idv = inv_dv[AX];
+    const PairCoef k = pair_coef<N>(make_float2((sh[1] * vc[alo * N + lo1] + sh[2] * vc[ahi * N + hi1] + sh[3]) * idv,
+                                                (sh[1] * vc[alo * N + lo2] + sh[2] * vc[ahi * N + hi2] + sh[3]) * idv));
+    const float2 a0 = k.a0, P = k.P, Q = k.Q, c0 = k.c0, cm = k.cm, cp = k.cp;
+    const bool whole = __ballot_sync(0xffffffffu, (v1 && k.s1 != 0) || (v2 && k.s2 != 0)) != 0u;
+    float2 r[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        r[q].x = (!RAGGED || v1) ? L1[q * ST] : 0.0f;
+        r[q].y = (!RAGGED || v2) ? L2[q * ST] : 0.0f;
+    }
+    float2 a_prev = r[0];  // a_{-1} = f_0 - 0
+    float2 ph1 = make_float2(0.0f, 0.0f), ph2 = ph1;  // phi_{q-1}, phi_{q-2}
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const float2 f = r[q];
+        const float2 a = q + 1 < N ? sub(r[q + 1], f) : neg(f);
+        const float2 f2 = add(f, f);
+        const float2 U = make_float2(fminf(a.x, f2.x), fminf(a.y, f2.y));
+        const float2 D = make_float2(fmaxf(a_prev.x, -f2.x), fmaxf(a_prev.y, -f2.y));
+        const float2 ph = fma(Q, D, fma(P, U, mul(a0, f)));
+        if (q == 1) r[0] = fma(cp, ph, fma(neg(cm), ph1, r[0]));
+        else if (q >= 2) r[q - 1] = fma(cp, ph, fma(cm, ph2, fma(c0, ph1, r[q - 1])));
+        ph2 = ph1;
+        ph1 = ph;
+        a_prev = a;
+    }
+    r[N - 1] = fma(cm, ph2, fma(neg(cp), ph1, r[N - 1]));
+    if (!whole) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (!RAGGED || v1) L1[q * ST] = r[q].x;
+            if (!RAGGED || v2) L2[q * ST] = r[q].y;
+        }
+    } else {
+        if (!RAGGED || v1) shift_store<N, ST, 0>(L1, r, k.s1, k.f1);
+        if (!RAGGED || v2) shift_store<N, ST, 1>(L2, r, k.s2, k.f2);
+        if (MOM) {
+            // the thread's own stores: read back the shifted lines
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                r[q].x = (!RAGGED || v1) ? L1[q * ST] : 0.0f;
+                r[q].y = (!RAGGED || v2) ? L2[q * ST] : 0.0f;
+            }
+        }
+    }
+    if (MOM) {
+        // centred sums S_p = sum_q xi_q^p f_q, xi_q = q - (N-1)/2, folded over
+        // the mirror pairs q, N-1-q (xi_{N-1-q} = -xi_q)
+        float2 s0 = make_float2(0.0f, 0.0f);
+        float S1x = 0.0f, S1y = 0.0f, S2x = 0.0f, S2y = 0.0f, S3x = 0.0f, S3y = 0.0f;
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            const float xi = (float)q - 0.5f * (float)(N - 1);
+            const float2 u = add(r[q], r[N - 1 - q]);
+            const float2 d = sub(r[q], r[N - 1 - q]);
+            s0 = add(s0, u);
+            S1x = fmaf(d.x, xi, S1x);
+            S1y = fmaf(d.y, xi, S1y);
+            S2x = fmaf(u.x, xi * xi, S2x);
+            S2y = fmaf(u.y, xi * xi, S2y);
+            S3x = fmaf(d.x, xi * xi * xi, S3x);
+            S3y = fmaf(d.y, xi * xi * xi, S3y);
+        }
+        float m[20];
+#pragma unroll
+        for (int o = 0; o < 20; ++o) m[o] = 0.0f;
+        const float cc = 0.5f * (float)(N - 1);
+        const float Sa[4] = {s0.x, S1x, S2x, S3x}, Sb[4] = {s0.y, S1y, S2y, S3y};
+        line_moments<AX>(m, Sa, (float)lo1 - cc, (float)hi1 - cc);
+        line_moments<AX>(m, Sb, (float)lo2 - cc, (float)hi2 - cc);
+        reduce_moments<float, warps(N)>(m, red, out, conv);
+    }
+}
+
+template <int N, bool RAGGED, bool MOM>
+__device__ __forceinline__ void sweep_axis(int axis, float* blk, const float* sh, const float* vc,
+                                           const float* inv_dv, int lo1, int hi1, int lo2, int hi2, bool v1, bool v2,
+                                           double* red, double* out, const MomConv& conv) {
+    if (axis == 0) sweep<N, 0, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
+    else if (axis == 1) sweep<N, 1, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
+    else sweep<N, 2, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
+}
+
+}  // namespace pair
+
+// One CTA per velocity block at a time (persistent over cells), as
+// velocity_kernel, with the FP32 two-lines-per-thread sweeps. Thread t of
+// warp w holds lines w 64 + lane and w 64 + 32 + lane (line = hi N + lo), so
+// each shared-memory instruction of a warp touches 32 consecutive lines.
+template <int N>
+__global__ void __launch_bounds__(pair::threads(N), pair::min_blocks(N)) velocity_pair_kernel(VelocityArgs a) {
+    constexpr int NTH = pair::threads(N);
+    constexpr bool RAGGED = (N * N) % 64 != 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int BLK = N * N * (N + 1);
+    float* const buf0 = reinterpret_cast<float*>(smem_raw);
+    float* const buf1 = buf0 + BLK;
+    double* red = reinterpret_cast<double*>(smem_raw + sizeof(float) * BLK * a.nbuf);
+    float* sh = reinterpret_cast<float*>(red + 20 * pair::warps(N) + 20);  // [20] shears of the cell
+    float* vc = sh + 20;                                                   // [3][N] cell-centre velocities
+    float* inv_dv = vc + 3 * N;                                            // [3]
+    float* f = reinterpret_cast<float*>(a.f);
+    constexpr long long V = (long long)N * N * N;
+    const bool two = a.nbuf == 2;
+    for (int q = threadIdx.x; q < 3 * N; q += NTH) {
+        const int ax = q / N, i = q % N;
+        vc[q] = (float)(a.vmin[ax] + (i + 0.5) * a.dv[ax]);
+    }
+    if (threadIdx.x < 3) inv_dv[threadIdx.x] = (float)(1.0 / a.dv[threadIdx.x]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m1 = warp * 64 + lane, m2 = m1 + 32;
+    const bool v1 = m1 < N * N, v2 = m2 < N * N;
+    const int lo1 = v1 ? m1 % N : 0, hi1 = v1 ? m1 / N : 0;
+    const int lo2 = v2 ? m2 % N : 0, hi2 = v2 ? m2 / N : 0;
+    long long cell = blockIdx.x;
+    auto prefetch = [](float* blk, const float* src) {
+        if constexpr (rows_tile<N, NTH>()) prefetch_block_rows<N, NTH>(blk, src);
+        else prefetch_block<float, N, NTH>(blk, src);
+    };
+    if (two && cell < a.ncell) prefetch(buf0, f + cell * V);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int it = 0; cell < a.ncell; cell += gridDim.x, ++it) {
+        float* blk = (two && (it & 1)) ? buf1 : buf0;
+        if (two) {
+            const long long nx = cell + gridDim.x;
+            if (nx < a.ncell) prefetch((it & 1) ? buf0 : buf1, f + nx * V);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            load_block<float, N, NTH>(blk, f + cell * V);
+        }
+        if (threadIdx.x < 20) sh[threadIdx.x] = (float)a.shears[cell * 20 + threadIdx.x];
+        __syncthreads();
+        double* out = a.mom_out ? a.mom_out + cell * 20 : nullptr;
+        for (int k = 0; k < a.nshear; ++k) {
+            const float* s = sh + 4 * k;
+            const int axis = (int)s[0];
+            if (out && k == a.nshear - 1)
+                pair::sweep_axis<N, RAGGED, true>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out,
+                                                  a.conv);
+            else
+                pair::sweep_axis<N, RAGGED, false>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out,
+                                                   a.conv);
+            __syncthreads();
+        }
+        if (groups_tile<N, NTH>() && a.vec) store_block_groups<N, NTH>(f + cell * V, blk);
+        else store_block<float, N, NTH>(f + cell * V, blk, a.vec != 0);
         __syncthreads();
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -510,6 +859,25 @@ static cudaError_t launch_velocity_n(const VelocityArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int N>
+static cudaError_t launch_velocity_pair(const VelocityArgs& a, cudaStream_t st) {
+    const int threads = pair::threads(N);
+    const size_t blk = sizeof(float) * N * N * (N + 1);
+    VelocityArgs b = a;
+    b.nbuf = 2 * blk <= 100 * 1024 ? 2 : 1;
+    b.vec = reinterpret_cast<uintptr_t>(a.f) % 16 == 0;
+    size_t smem = blk * b.nbuf + sizeof(double) * (20 * pair::warps(N) + 20) + sizeof(float) * (20 + 3 * N + 3);
+    cudaFuncSetAttribute(velocity_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_pair_kernel<N>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > a.ncell) grid = a.ncell;
+    velocity_pair_kernel<N><<<(unsigned)grid, threads, smem, st>>>(b);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T, int N>
 static cudaError_t launch_moments_n(const MomentArgs& a, cudaStream_t st) {
     const int threads = ((N * N + 31) / 32) * 32;
@@ -553,7 +921,14 @@ cudaError_t launch_velocity(const VelocityArgs& a, int nvdim, int precision, cud
         if (e != cudaSuccess) return e;
     }
     if (precision == 64) { VL_DISPATCH_N(launch_velocity_n, double, a.nv, a, st); }
-    VL_DISPATCH_N(launch_velocity_n, float, a.nv, a, st);
+    switch (a.nv) {
+        case 8: return launch_velocity_pair<8>(a, st);
+        case 12: return launch_velocity_pair<12>(a, st);
+        case 16: return launch_velocity_pair<16>(a, st);
+        case 20: return launch_velocity_pair<20>(a, st);
+        case 24: return launch_velocity_pair<24>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_moments(const MomentArgs& a, int nvdim, int precision, cudaStream_t st) {

@@ -162,6 +162,41 @@ def test_velocity_pass_and_fused_moments(gpu, orc, precision, nshear, nv):
     r.close()
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nv", [8, 12, 16, 20, 24])
+def test_velocity_pass_whole_cell_shifts(gpu, orc, precision, nv):
+    """Displacements of several cells and beyond the box (Sec. 2.1's sweep at
+    any displacement: whole cells move, what leaves the box piles up in its
+    last cell), in both directions, against the oracle."""
+    from gpu_util import AbiRunner
+    from paper_2109_06743_gb300 import abi
+    cfg = small_harris(nx=4, ny=3, nv=nv, precision=precision)
+    V = nv ** 3
+    f0 = [cast(W.random_blocks((cfg.ncell, V), 230 + k) ** 4, precision) for k in range(2)]
+    eb = W.random_fields(cfg.ncell, 17, e_scale=4.0, b_scale=2.0)
+    eb[0, :3] = (60.0, -45.0, 30.0)  # electrons: every line beyond the box
+    eb[1, 3:] = 0.0                   # pure electric kick
+    eb[2, :3] = 0.0                   # pure rotation, about 2.4 rad for electrons
+    r = AbiRunner(cfg, f0, eb=eb)
+    g = oracle_grid(orc, cfg)
+    dt = 0.05
+    for k, sp in enumerate(cfg.species):
+        mom = r.mom()
+        abi.pfc_advect_v(r.ctx, k, dt, mom)
+        ref = f0[k].copy()
+        s = oracle_species(orc, sp)
+        orc.advect_velocity(ref, g, s, eb, dt, 5)
+        got = r.f_np(k)
+        tol = (1e-12 if precision == 64 else 1e-5) * ref.max()
+        assert np.abs(got - ref).max() <= tol, (k, np.abs(got - ref).max(), tol)
+        np.testing.assert_allclose(got.sum(axis=1), f0[k].sum(axis=1), rtol=1e-13 if precision == 64 else 2e-6)
+        r.sync()
+        m_ref = orc.moments(np.ascontiguousarray(got), g, s)
+        scale = abs_moment_scale(got, sp)
+        assert np.all(np.abs(mom.cpu().numpy() - m_ref) <= (1e-12 if precision == 64 else 1e-5) * scale)
+    r.close()
+
+
 MONO = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1),
         (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1),
         (0, 1, 2), (0, 0, 3)]
