@@ -149,10 +149,22 @@ ISSUED_OPS_GRAM_DF = 7
 # Gram sums (2).
 ISSUED_OPS_MOMENT_64 = 5
 ISSUED_OPS_GRAM_64 = 2
-# DRAM bytes per cell of one fit launch (one species), by kernel and velocity
-# grid, from ncu captures of the current kernels (targets, coefficients,
-# status and the kernel's local memory); a grid not captured gives None.
-NEWTON_DRAM_BYTES_PER_CELL = {}
+# DRAM bytes per cell of one fit launch (one species), by kernel (FP64 or
+# not) and velocity grid, from ncu captures of the current kernels on the
+# 256 x 128 Harris sheet (dram__bytes_read.sum + dram__bytes_write.sum over
+# 32768 cells; scaled by the cell count, as the traffic is per cell): the
+# double-float kernel warm-started, 39.58 MB (targets, coefficients, status,
+# predictions and its local memory), the FP64 kernel cold-started, 8.20 MB
+# (its coefficient writes stay in L2 during the launch). A grid not captured
+# gives None.
+# timed runs of the end-to-end leg (the median is reported)
+E2E_REPS = 3
+NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.578880e6 / 32768, (True, 16): 8.204032e6 / 32768}
+# Bytes a fit launch must move per cell: the 20 raw moments (read), the fluid
+# state (10 doubles read and written), both Maxwellians' 16 coefficients
+# (written), the status pair and, warm-started, the network's 20 predictions.
+NEWTON_ALGORITHMIC_BYTES_PER_CELL = 20 * 8 + 2 * 10 * 8 + 2 * 16 * 8 + 2 * 4
+NEWTON_WARM_BYTES_PER_CELL = 20 * 4
 
 
 def measured_alu_peaks(device):
@@ -197,8 +209,10 @@ def newton_roofline(cfg, stats, fit_ms, launches, alu, fp64=False):
     method = (METHOD_OPS_MOMENT * em + METHOD_OPS_GRAM * eg) * n3
     achieved = method / secs / 1e12
     per_cell = NEWTON_DRAM_BYTES_PER_CELL.get((fp64, cfg.species[0].nv[0]))
+    alg = NEWTON_ALGORITHMIC_BYTES_PER_CELL + (0 if fp64 else NEWTON_WARM_BYTES_PER_CELL)
     out = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (%s pipe)" % pipe,
            "frac": achieved / peak, "traffic": None if per_cell is None else per_cell * cfg.ncell,
+           "algorithmic_bytes_per_launch": alg * cfg.ncell,
            "peak_kind": "measured (vl_fma_peak)",
            "method_ops_per_launch": method / max(1, launches), "method_frac": achieved / peak,
            "issued_ops_per_launch": issued / max(1, launches), "issued_frac": issued / secs / 1e12 / peak,
@@ -727,22 +741,29 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
         host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
         for h, f in zip(host, sim.f):
             h.copy_(f)
-        barrier_sync()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.host_streams_after(e0)
-        with torch.cuda.stream(stream):
-            for _ in range(e2e_steps):
-                sim.step_through_host(host, use_mlp=use_mlp)
-            sim.wait_host()
-        e1.record(stream)
-        barrier_sync()
-        et = slowest(e0.elapsed_time(e1) / 1e3, dist, device)
+        # three timed runs of e2e_steps steps each; the median run is the
+        # figure (the host link is shared with the node's other GPUs, and one
+        # run can meet their traffic), every run is listed
+        reps = []
+        for _ in range(E2E_REPS):
+            barrier_sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.host_streams_after(e0)
+            with torch.cuda.stream(stream):
+                for _ in range(e2e_steps):
+                    sim.step_through_host(host, use_mlp=use_mlp)
+                sim.wait_host()
+            e1.record(stream)
+            barrier_sync()
+            reps.append(slowest(e0.elapsed_time(e1) / 1e3, dist, device))
+        et = sorted(reps)[len(reps) // 2]
         nbytes = sum(f.numel() * f.element_size() for f in sim.f)
         link = host_link(host, sim.f_spare or sim.f)
         e2e = {"value": job_rate(cells, e2e_steps, world, et), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_per_step": 1e3 * et / e2e_steps,
+               "runs_ms_per_step": [1e3 * t / e2e_steps for t in reps], "run_reported": "median of %d" % E2E_REPS,
                "host_link": link,
                "copy_bound_value": cells / (link["step_copy_ms_at_roof"] / 1e3)}
         del host
