@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "block_moments.cuh"
+#include "f32x2.cuh"
 
 namespace vl {
 
@@ -467,19 +468,11 @@ __global__ void __launch_bounds__(vel_threads(N), vel_min_blocks(N, sizeof(T))) 
 
 namespace pair {
 
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) {
-    unsigned long long ua, ub, d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(ua), "l"(ub));
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
-    return r;
-}
-__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+using x2::add;
+using x2::fma;
+using x2::mul;
+using x2::neg;
+using x2::sub;
 
 constexpr int threads(int n) { return ((n * n / 2 + 31) / 32) * 32; }
 constexpr int warps(int n) { return threads(n) / 32; }
