@@ -824,6 +824,48 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "fp64_form": fp64}
 
 
+def launch_fixed_cost(device, step_ms, per_launch_ms, reps=50):
+    """What batching the species into one launch could save (the fused
+    sweep's multi-species batching): the fixed cost of one per-species
+    launch -- launch, per-CTA set-up, and a last partial wave -- measured as
+    the whole duration of the same pass on a 16 x 16 window (the workload's
+    dx, dv and dt), where one partial wave of persistent CTAs does all the
+    work. CUDA events around each call (the velocity pass's call includes its
+    shear set-up kernel); the bound is one such cost per pass and step for the
+    second species, against the full step."""
+    import numpy as np
+    import torch
+
+    from paper_2109_06743_gb300 import abi
+    from paper_2109_06743_gb300.driver import Simulation
+    cfg = make_cfg("harris_512x256_v16", precision=32, sub=(16, 16))
+    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device)
+    st = sim.stream
+    out = {"window": "16x16 x 16^3, one species, the workload's dx, dv and dt", "reps": reps}
+    for name in ("xy_sweep", "v_pass"):
+        evs = []
+        with torch.cuda.stream(st):
+            for r in range(reps + 3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                if name == "xy_sweep":
+                    abi.pfc_advect_xy(sim.ctx, 0, cfg.dt, sim.f_spare[0], st)
+                    sim.f[0], sim.f_spare[0] = sim.f_spare[0], sim.f[0]
+                else:
+                    abi.pfc_advect_v(sim.ctx, 0, cfg.dt, None, st)
+                e1.record(st)
+                if r >= 3:
+                    evs.append((e0, e1))
+        torch.cuda.synchronize()
+        us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        out[name + "_us"] = us[len(us) // 2]
+        if per_launch_ms.get(name):
+            out[name + "_full_size_ms_per_species"] = per_launch_ms[name]
+    sim.close()
+    out["batching_bound_pct_of_step"] = 100.0 * 1e-3 * (out["xy_sweep_us"] + out["v_pass_us"]) / step_ms
+    return out
+
+
 def shear_ablation(device, steps=100):
     """The velocity splitting read two ways (Sec. 2.1's backsubstitution):
     the exact five-shear factorisation of the Boris map against the plain
@@ -944,6 +986,8 @@ def main():
         if rank == 0:
             nested[LANDAU] = landau_block(200, 3)
             line["shear_ablation"] = shear_ablation(device)
+            line["species_launch_fixed_cost"] = launch_fixed_cost(
+                device, res["ms_per_step"], {k: v["ms_per_launch"] for k, v in res["hbm_phases"].items()})
         line["workloads"] = nested
     if rank == 0:
         print(json.dumps(line))

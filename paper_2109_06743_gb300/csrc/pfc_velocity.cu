@@ -583,8 +583,7 @@ __device__ __forceinline__ void line_moments(float (&m)[20], const float (&S)[4]
 // formed from the registers and reduced over the CTA into out.
 template <int N, int AX, bool RAGGED, bool MOM>
 __device__ __forceinline__ void sweep(float* blk, const float* sh, const float* vc, const float* inv_dv, int lo1,
-                                      int hi1, int lo2, int hi2, bool v1, bool v2, double* red, double* out,
-                                      const MomConv& conv) {
+                                      int hi1, int lo2, int hi2, bool v1, bool v2, float (&m)[20]) {
     constexpr int ST = AX == 0 ? 1 : (AX == 1 ? N + 1 : N * (N + 1));
     constexpr int alo = AX == 0 ? 1 : 0, ahi = AX == 2 ? 1 : 2;
     auto start = [](int lo, int hi) {
@@ -656,24 +655,20 @@ __device__ __forceinline__ void sweep(float* blk, const float* sh, const float* 
             S3x = fmaf(d.x, xi * xi * xi, S3x);
             S3y = fmaf(d.y, xi * xi * xi, S3y);
         }
-        float m[20];
-#pragma unroll
-        for (int o = 0; o < 20; ++o) m[o] = 0.0f;
         const float cc = 0.5f * (float)(N - 1);
         const float Sa[4] = {s0.x, S1x, S2x, S3x}, Sb[4] = {s0.y, S1y, S2y, S3y};
         line_moments<AX>(m, Sa, (float)lo1 - cc, (float)hi1 - cc);
         line_moments<AX>(m, Sb, (float)lo2 - cc, (float)hi2 - cc);
-        reduce_moments<float, warps(N)>(m, red, out, conv);
     }
 }
 
 template <int N, bool RAGGED, bool MOM>
 __device__ __forceinline__ void sweep_axis(int axis, float* blk, const float* sh, const float* vc,
                                            const float* inv_dv, int lo1, int hi1, int lo2, int hi2, bool v1, bool v2,
-                                           double* red, double* out, const MomConv& conv) {
-    if (axis == 0) sweep<N, 0, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
-    else if (axis == 1) sweep<N, 1, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
-    else sweep<N, 2, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out, conv);
+                                           float (&m)[20]) {
+    if (axis == 0) sweep<N, 0, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, m);
+    else if (axis == 1) sweep<N, 1, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, m);
+    else sweep<N, 2, RAGGED, MOM>(blk, sh, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, m);
 }
 
 }  // namespace pair
@@ -730,12 +725,15 @@ __global__ void __launch_bounds__(pair::threads(N), pair::min_blocks(N)) velocit
         for (int k = 0; k < a.nshear; ++k) {
             const float* s = sh + 4 * k;
             const int axis = (int)s[0];
-            if (out && k == a.nshear - 1)
-                pair::sweep_axis<N, RAGGED, true>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out,
-                                                  a.conv);
-            else
-                pair::sweep_axis<N, RAGGED, false>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, red, out,
-                                                   a.conv);
+            float m[20];
+#pragma unroll
+            for (int o = 0; o < 20; ++o) m[o] = 0.0f;
+            if (out && k == a.nshear - 1) {
+                pair::sweep_axis<N, RAGGED, true>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, m);
+                reduce_moments<float, pair::warps(N)>(m, red, out, a.conv);
+            } else {
+                pair::sweep_axis<N, RAGGED, false>(axis, blk, s, vc, inv_dv, lo1, hi1, lo2, hi2, v1, v2, m);
+            }
             __syncthreads();
         }
         if (groups_tile<N, NTH>() && a.vec) store_block_groups<N, NTH>(f + cell * V, blk);
