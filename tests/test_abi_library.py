@@ -103,3 +103,17 @@ def test_static_pass_refuses_bad_pointers_before_any_launch(lib):
 
 def test_sync_status_rejects_a_missing_context(lib):
     assert lib.vl_sync_status(None, None) == abi.VL_EINVAL
+
+
+def test_fma_peak_rejects_bad_arguments_on_the_host(lib):
+    """vl_fma_peak refuses a precision other than 32 or 64, missing pointers
+    and a misaligned sink before any device work (no GPU needed)."""
+    import ctypes
+    out = ctypes.c_double(-1.0)
+    sink = ctypes.c_void_p(4096)
+    assert lib.vl_fma_peak(48, ctypes.byref(out), sink, None) == abi.VL_EINVAL
+    assert b"precision" in lib.vl_last_error(None)
+    assert lib.vl_fma_peak(32, None, sink, None) == abi.VL_EINVAL
+    assert lib.vl_fma_peak(64, ctypes.byref(out), None, None) == abi.VL_EINVAL
+    assert lib.vl_fma_peak(32, ctypes.byref(out), ctypes.c_void_p(4100), None) == abi.VL_EINVAL
+    assert b"aligned" in lib.vl_last_error(None)
