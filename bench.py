@@ -741,7 +741,8 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
         host = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in sim.f]
         for h, f in zip(host, sim.f):
             h.copy_(f)
-        # E2E_REPS timed runs of e2e_steps steps each; the fastest run is the
+        # E2E_REPS timed runs of e2e_steps steps each (the first step of a run
+        # also fills the copy pipeline); the fastest run is the
         # figure, as for the host link's own rates (the link and the host's
         # memory are shared with the node's other GPUs, whose traffic can slow
         # any number of runs), and every run is listed
@@ -965,7 +966,9 @@ def main():
     affinity = pin_host_to_gpu(local)
     alu = measured_alu_peaks(device)
     extra = not args.no_extra and args.workload == "harris_512x256_v16"
-    res = measure_2d3v(args.workload, device, alu, args.steps, args.warmup, 0 if args.no_e2e else min(args.steps, 10),
+    # the end-to-end leg times the same K steps as the device figure (each
+    # run; at most 50)
+    res = measure_2d3v(args.workload, device, alu, args.steps, args.warmup, 0 if args.no_e2e else min(args.steps, 50),
                        max(1, min(args.steps, 5)), args.fp64_steps, not args.no_cpu, not args.no_all_cores,
                        harvest_steps=args.harvest_steps, train_from=args.train_from, no_mlp=args.no_mlp, dist=dist,
                        world=world, gpu_index=local,
