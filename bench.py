@@ -987,6 +987,11 @@ def main():
         nested["asym_1024x512_v12"] = measure_2d3v(
             "asym_1024x512_v12", device, alu, 5, 2, 3, 3, 3 if args.fp64_steps else 0, not args.no_cpu, False,
             dist=dist, world=world, gpu_index=local)
+        # the 20^3 Harris run whose fits train the transfer network (no
+        # accuracy window: its oracle step would take minutes on one core)
+        nested["harris_128x64_v20"] = measure_2d3v(
+            "harris_128x64_v20", device, alu, 10, 3, 10, 3, 3 if args.fp64_steps else 0, False, False,
+            dist=dist, world=world, gpu_index=local)
         if rank == 0:
             nested[LANDAU] = landau_block(200, 3)
             line["shear_ablation"] = shear_ablation(device)
