@@ -34,13 +34,16 @@ def _train(ctx, buf, n, train_steps, batch, lr, seed, stream):
     return np.asarray(losses)
 
 
-def train_warm_start(name, device, harvest_steps=24, train_steps=3000, batch=4096, lr=2e-3):
+def train_warm_start(name, device, harvest_steps=24, train_steps=None, batch=4096, lr=2e-3):
     """Harvest (inputs, eta* - eta_0) samples from the converged fits of
     harvest_steps cold-started steps of the named workload, train the
     warm-start network on the GPU with the project's own kernels (Adam,
-    learning rate lr stepped down by LR_SCHEDULE), and return its weights and
-    a summary (sample count, first and last losses, seconds)."""
+    train_steps steps, by default workloads.TRAIN_STEPS of the run or 3000;
+    learning rate lr stepped down by LR_SCHEDULE), and return its weights
+    and a summary (sample count, first and last losses, seconds)."""
     t0 = time.perf_counter()
+    if train_steps is None:
+        train_steps = W.TRAIN_STEPS.get(name, 3000)
     cfg = W.named(name, precision=32)
     sim = Simulation(cfg, W.initial_state(cfg, np.float32), None, W.initial_yee(cfg), device=device)
     cap = harvest_steps * 4 * cfg.ncell

@@ -508,6 +508,11 @@ NAMED = {
 TRAIN_FROM = {"harris_512x256_v16": "harris_128x64_v16", "harris_256x128_v16": "harris_128x64_v16",
               "harris_128x64_v20": "harris_128x64_v20", "harris_128x64_v16": "harris_128x64_v16",
               "asym_1024x512_v12": "asym_256x128_v12", "asym_256x128_v12": "asym_256x128_v12"}
+# Adam steps of the network's training, by training run (default 3000). The
+# asymmetric sheet's fits are harder to predict: 10000 steps bring its fit
+# from 54-58 to 44-52 ms per step at 1024 x 512 (two seeds each); on the
+# Harris sheet more steps lower the loss but not the fit time.
+TRAIN_STEPS = {"asym_256x128_v12": 10000}
 
 
 def named(name, precision=32, sub=None) -> Config:
