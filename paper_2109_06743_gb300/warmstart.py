@@ -4,6 +4,7 @@ cell's target moments to a warm start of its Newton fit, Sec. 2.2 with
 Algorithm 1's fit). The samples are harvested by the Newton kernel from its
 converged fits; normalisation, training (BF16 tensor-core GEMMs, FP32
 accumulation, Adam) and inference run in the library's kernels."""
+import math
 import time
 
 import numpy as np
@@ -22,15 +23,19 @@ LR_SCHEDULE = ((0.5, 1.0), (1.0 / 3.0, 0.3), (1.0 / 6.0, 0.1))
 
 
 def _train(ctx, buf, n, train_steps, batch, lr, seed, stream):
-    """Adam steps in the segments of LR_SCHEDULE; the losses of every step."""
+    """Adam steps in the segments of LR_SCHEDULE (segment ends at the
+    cumulative shares, rounded up, so that a short run starts at the full
+    rate); the losses of every step."""
     losses = []
-    left = train_steps
+    done, cum = 0, 0.0
     for k, (share, factor) in enumerate(LR_SCHEDULE):
-        steps = left if k == len(LR_SCHEDULE) - 1 else min(left, int(round(share * train_steps)))
+        cum += share
+        end = train_steps if k == len(LR_SCHEDULE) - 1 else min(train_steps, math.ceil(cum * train_steps - 1e-9))
+        steps = end - done
         if steps > 0:
             losses += list(abi.mlp_train(ctx, buf, n, steps, batch=batch, lr=lr * factor, seed=seed + k,
                                          record_loss=True, stream=stream))
-        left -= steps
+        done = max(done, end)
     return np.asarray(losses)
 
 

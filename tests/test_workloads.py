@@ -25,3 +25,36 @@ def test_asymmetric_yee_divergence_free_and_reproducible():
     div = (np.roll(bx[:cfg.ny], -1, axis=1) - bx[:cfg.ny]) / cfg.dx + (by[1:] - by[:-1]) / cfg.dy
     assert np.abs(div).max() < 1e-10 * np.abs(bx).max() / cfg.dx
     assert np.all(y1[5][:cfg.ny] == cfg.bguide)
+
+
+def test_training_schedule_covers_every_step(monkeypatch):
+    """warmstart._train splits the Adam steps into the segments of
+    LR_SCHEDULE in order: the segments add up to the requested steps, each
+    runs at lr times its factor with its own seed, and the losses of all
+    steps come back in order (host logic; the training call is stubbed)."""
+    import numpy as np
+    from paper_2109_06743_gb300 import abi, warmstart
+    calls = []
+
+    def fake_train(ctx, buf, n, steps, batch=4096, lr=1e-3, seed=0, record_loss=False, stream=None):
+        calls.append((steps, lr, seed))
+        start = sum(c[0] for c in calls[:-1])
+        return np.arange(start, start + steps, dtype=float)
+
+    monkeypatch.setattr(abi, "mlp_train", fake_train)
+    for total in (3000, 10000, 7, 1):
+        calls.clear()
+        losses = warmstart._train(None, None, 1, total, 4096, 2e-3, 100, None)
+        assert sum(c[0] for c in calls) == total
+        assert np.array_equal(losses, np.arange(total, dtype=float))
+        factors = [f for _, f in warmstart.LR_SCHEDULE]
+        assert all(c[0] > 0 for c in calls)
+        used = [(s, lr) for s, lr, _ in calls]
+        # the rates never rise and start at lr
+        assert used[0][1] == 2e-3 and all(a[1] >= b[1] for a, b in zip(used, used[1:]))
+        assert len({c[2] for c in calls}) == len(calls)
+    calls.clear()
+    warmstart._train(None, None, 1, 3000, 4096, 2e-3, 100, None)
+    assert [c[0] for c in calls] == [1500, 1000, 500]
+    assert np.allclose([c[1] for c in calls], [2e-3 * f for f in factors])
+    assert W.TRAIN_STEPS.get("asym_256x128_v12") == 10000 and "harris_128x64_v16" not in W.TRAIN_STEPS
