@@ -158,7 +158,7 @@ ISSUED_OPS_GRAM_64 = 2
 # (its coefficient writes stay in L2 during the launch). A grid not captured
 # gives None.
 # timed runs of the end-to-end leg (the fastest is reported, all are listed)
-E2E_REPS = 5
+E2E_REPS = 8
 NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.578880e6 / 32768, (True, 16): 8.204032e6 / 32768}
 # Bytes a fit launch must move per cell: the 20 raw moments (read), the fluid
 # state (10 doubles read and written), both Maxwellians' 16 coefficients
@@ -595,11 +595,12 @@ def hbm_rows(phase_ms, count, per_launch_cells, bytes_per_cell=8):
     return rows
 
 
-def host_link(host, dev, reps=3):
+def host_link(host, dev, reps=3, both_only=False):
     """Pinned host <-> device copy rates with plain cudaMemcpyAsync (torch
     copy_ of pinned tensors, one stream per direction): host to device
     alone, device to host alone, and both at once; the roof of the
-    end-to-end leg, which moves f both ways every step."""
+    end-to-end leg, which moves f both ways every step. both_only: only
+    the rate each way with both directions at once (GB/s)."""
     import torch
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     nbytes = sum(h.numel() * h.element_size() for h in host)
@@ -628,6 +629,8 @@ def host_link(host, dev, reps=3):
             best = t if best is None else min(best, t)
         return best
 
+    if both_only:
+        return nbytes / run(True, True) / 1e9
     t_h2d = run(True, False)
     t_d2h = run(False, True)
     t_both = run(True, True)
@@ -745,9 +748,12 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
         # also fills the copy pipeline); the fastest run is the
         # figure, as for the host link's own rates (the link and the host's
         # memory are shared with the node's other GPUs, whose traffic can slow
-        # any number of runs), and every run is listed
-        reps = []
+        # any number of runs), and every run is listed with the both-ways copy
+        # rate of the same buffers measured right before it
+        reps, link_before = [], []
         for _ in range(E2E_REPS):
+            barrier_sync()
+            link_before.append(host_link(host, sim.f_spare or sim.f, reps=1, both_only=True))
             barrier_sync()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -766,6 +772,7 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
         e2e = {"value": job_rate(cells, e2e_steps, world, et), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": e2e_steps, "ms_per_step": 1e3 * et / e2e_steps,
                "runs_ms_per_step": [1e3 * t / e2e_steps for t in reps], "run_reported": "fastest of %d" % E2E_REPS,
+               "runs_link_GBps_each_way_before": link_before,
                "host_link": link,
                "copy_bound_value": cells / (link["step_copy_ms_at_roof"] / 1e3)}
         del host
