@@ -23,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import abi
+from . import workloads as W
 
 
 class Simulation:
@@ -90,6 +91,7 @@ class Simulation:
             for k in range(len(cfg.species)):
                 abi.moment_fit_wide(self.ctx, k, wide_fit)
         self.time = 0.0
+        self.nstep = 0
 
     def close(self):
         if self.ctx is not None:
@@ -175,6 +177,7 @@ class Simulation:
             abi.maxwell_step(ctx, 0.5 * dt, None if self.fit else self.mom_t, s)
         mark(None)
         self.time += dt
+        self.nstep += 1
 
     def graph(self, steps, use_mlp=False):
         """A CUDA graph of `steps` time steps on the solver's stream, to be
@@ -264,6 +267,108 @@ class Simulation:
         for evs in getattr(self, "_d2h_done", None) or []:
             for ev in evs or []:
                 self.stream.wait_event(ev)
+
+    # -- checkpoint and resume ------------------------------------------------------
+    def save(self, path):
+        """Write everything that determines the later steps to ``path`` (an
+        .npz file): f of every species, the fluid state, the moments of f at t
+        (from the last exchange: the next step's Q^t), the Yee and the
+        cell-centred fields, the time and step count, the warm-start network's
+        parameters (when the context has them) and the configuration. A
+        Simulation made by ``resume`` from it continues bit for bit as this
+        one would. Synchronises the stream."""
+        cfg = self.cfg
+        self.stream.synchronize()
+        arrays = {"config": np.array(W.config_to_json(cfg)), "time": np.array(self.time),
+                  "nstep": np.array(self.nstep), "fit": np.array(self.fit),
+                  "fluid": self.fluid.cpu().numpy(), "eb": self.eb.cpu().numpy()}
+        try:
+            arrays["mlp"] = abi.mlp_get_weights(self.ctx)
+        except abi.VlasovError:
+            pass  # the context has no network
+        for k in range(len(cfg.species)):
+            arrays["f%d" % k] = self.f[k].cpu().numpy()
+            arrays["mom_t%d" % k] = self.mom_t[k].cpu().numpy()
+        if self.yee is not None:
+            arrays["yee"] = self.yee.cpu().numpy()
+        np.savez(path, **arrays)
+
+    @classmethod
+    def resume(cls, path, device="cuda", stream=None, fused_xy=True, wide_fit=None):
+        """A Simulation in the state ``save`` wrote to ``path``."""
+        import torch
+
+        z = np.load(path)
+        cfg = W.config_from_json(str(z["config"]))
+        ns = len(cfg.species)
+        sim = cls(cfg, [z["f%d" % k] for k in range(ns)], list(z["fluid"]), z["yee"] if "yee" in z else None,
+                  device=device, stream=stream, fit=bool(z["fit"]), fused_xy=fused_xy, wide_fit=wide_fit)
+        with torch.cuda.stream(sim.stream):
+            for k in range(ns):
+                sim.mom_t[k].copy_(torch.as_tensor(z["mom_t%d" % k]))
+            sim.eb.copy_(torch.as_tensor(z["eb"]))
+            if "yee" in z:
+                # the constructor's zero-length field step may turn -0.0 into +0.0
+                sim.yee.copy_(torch.as_tensor(z["yee"]))
+        if "mlp" in z:
+            abi.mlp_set_weights(sim.ctx, z["mlp"])
+        sim.time = float(z["time"])
+        sim.nstep = int(z["nstep"])
+        return sim
+
+    # -- per-step diagnostics ------------------------------------------------------
+    def diagnostics(self):
+        """Step, time, mass per species (m times the integral of n), energy
+        partition and total, the reconnected flux (2D3V) and the fit counters
+        accumulated since the last reset (Newton iterations, fallbacks,
+        clipped cells, invalid targets). Synchronises the stream."""
+        cfg = self.cfg
+        kin, ee, eb = self.energies()
+        area = cfg.dx * (cfg.dy if cfg.nvdim == 3 else 1.0)
+        st = self.stats()
+        d = {"step": self.nstep, "time": self.time,
+             "mass": [float(m[:, 0].sum().item()) * area * sp.m for sp, m in zip(cfg.species, self.mom_t)],
+             "kinetic_thermal": [float(x) for x in kin], "electric": float(ee), "magnetic": float(eb),
+             "total_energy": float(sum(kin) + ee + eb),
+             "newton_iterations": st[0], "newton_fallbacks": st[1], "clipped_cells": st[2], "invalid_fits": st[3]}
+        if cfg.nvdim == 3:
+            # on the sheet's X line (the B_x null of an asymmetric sheet)
+            d["reconnected_flux"] = float(self.reconnected_flux(W.x_line(cfg) if hasattr(cfg, "kind") else 0.0))
+        return d
+
+    def run(self, steps, use_mlp=False, log=None, every=1):
+        """Advance ``steps`` steps. With ``log`` (a path, opened for appending,
+        or a text file), write one JSON line of ``diagnostics()`` every
+        ``every`` steps and after the last one, with the fit counters of the
+        steps since the previous line and the mean step time over them (CUDA
+        events on the solver's stream, diagnostics excluded)."""
+        import json
+
+        torch = self.torch
+        fh = open(log, "a") if isinstance(log, (str, bytes)) or hasattr(log, "__fspath__") else log
+        try:
+            if fh is not None:
+                abi.vl_reset_stats(self.ctx, self.stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            since = 0
+            for i in range(steps):
+                self.step(use_mlp=use_mlp)
+                since += 1
+                if fh is not None and (since == every or i == steps - 1):
+                    e1.record(self.stream)
+                    e1.synchronize()
+                    d = self.diagnostics()
+                    d["ms_per_step"] = e0.elapsed_time(e1) / since
+                    fh.write(json.dumps(d) + "\n")
+                    fh.flush()
+                    abi.vl_reset_stats(self.ctx, self.stream)
+                    since = 0
+                    e0.record(self.stream)
+        finally:
+            if fh is not None and fh is not log:
+                fh.close()
 
     # -- host-side views (diagnostics and tests) --------------------------------
     def f_host(self, k):

@@ -87,6 +87,37 @@ class Config:
         return sum(self.ncell * s.vblock for s in self.species)
 
 
+def config_to_json(cfg: Config) -> str:
+    """The configuration as a JSON string (checkpoints): the dataclass
+    fields, and the attributes the workload builders add beside them (the
+    initial state's parameters, a species' temperature)."""
+    import json
+    fields = {f.name for f in dataclasses.fields(Config)}
+    sfields = {f.name for f in dataclasses.fields(SpeciesCfg)}
+    d = dataclasses.asdict(cfg)
+    d["extra"] = {k: v for k, v in vars(cfg).items() if k not in fields}
+    for sd, sp in zip(d["species"], cfg.species):
+        sd["extra"] = {k: v for k, v in vars(sp).items() if k not in sfields}
+    return json.dumps(d, sort_keys=True, default=lambda o: o.item() if hasattr(o, "item") else str(o))
+
+
+def config_from_json(text: str) -> Config:
+    """Inverse of config_to_json."""
+    import json
+    d = json.loads(text)
+    species = []
+    for sd in d.pop("species"):
+        sp = SpeciesCfg(sd["name"], sd["q"], sd["m"], tuple(sd["nv"]), tuple(sd["vmin"]), tuple(sd["vmax"]))
+        for k, v in sd.get("extra", {}).items():
+            setattr(sp, k, v)
+        species.append(sp)
+    extra = d.pop("extra", {})
+    cfg = Config(species=species, **d)
+    for k, v in extra.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
 # ----------------------------------------------------------------- Landau ---
 
 def landau(nx=64, nv=32, vmax=6.0, alpha=0.01, k=0.5, dt=0.05, steps=200,

@@ -1,7 +1,9 @@
 """Pins of the synthetic input generators: the asymmetric sheet is in exact
 pressure balance with the stated far fields, its magnetic field is
-discretely divergence free, and the counter-hash noise is reproducible."""
+discretely divergence free, and the counter-hash noise is reproducible; the
+configuration's JSON form (checkpoints) round-trips."""
 import numpy as np
+import pytest
 
 from paper_2109_06743_gb300 import workloads as W
 
@@ -58,3 +60,19 @@ def test_training_schedule_covers_every_step(monkeypatch):
     assert [c[0] for c in calls] == [1500, 1000, 500]
     assert np.allclose([c[1] for c in calls], [2e-3 * f for f in factors])
     assert W.TRAIN_STEPS.get("asym_256x128_v12") == 10000 and "harris_128x64_v16" not in W.TRAIN_STEPS
+
+
+@pytest.mark.parametrize("make", [lambda: W.landau(), lambda: W.two_stream(precision=32),
+                                  lambda: W.named("harris_128x64_v20", precision=64),
+                                  lambda: W.named("harris_512x256_v16", sub=(64, 32)),
+                                  lambda: W.named("asym_1024x512_v12")])
+def test_config_json_round_trip(make):
+    """checkpoints store the configuration as JSON: every field and every
+    attribute the builders add comes back"""
+    cfg = make()
+    cfg.fit_tol = 3e-12
+    back = W.config_from_json(W.config_to_json(cfg))
+    assert back == cfg and vars(back) == vars(cfg)
+    for a, b in zip(back.species, cfg.species):
+        assert vars(a) == vars(b) and isinstance(a.nv, tuple) and a.dv == b.dv
+    assert back.phase_cells() == cfg.phase_cells()
