@@ -159,7 +159,7 @@ ISSUED_OPS_GRAM_64 = 2
 # gives None.
 # timed runs of the end-to-end leg (the fastest is reported, all are listed)
 E2E_REPS = 8
-NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.578880e6 / 32768, (True, 16): 8.204032e6 / 32768}
+NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.257856e6 / 32768, (True, 16): 8.204032e6 / 32768}
 # Bytes a fit launch must move per cell: the 20 raw moments (read), the fluid
 # state (10 doubles read and written), both Maxwellians' 16 coefficients
 # (written), the status pair and, warm-started, the network's 20 predictions.
