@@ -643,7 +643,7 @@ def host_link(host, dev, reps=3, both_only=False):
 
 def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_steps, accuracy, all_cores,
                  harvest_steps=24, train_from=None, no_mlp=False, dist=None, world=1, gpu_index=0,
-                 transfer_from=None, transfer_samples=0):
+                 transfer_from=None, transfer_samples=0, fused_xy=True):
     """One 2D3V workload: the FP32+MLP form timed over `steps` steps (CUDA
     events per phase, clocks sampled), its roofline, the same steps with
     cold-started fits, optionally the warm-start network trained on another
@@ -661,7 +661,7 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
     mlp_w, mlp_info = (None, None) if no_mlp else train_warm_start(train_from, device, harvest_steps=harvest_steps)
     use_mlp = mlp_w is not None
     cfg = make_cfg(name, precision=32)
-    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device)
+    sim = Simulation(cfg, initial_state(cfg, np.float32), None, initial_yee(cfg), device=device, fused_xy=fused_xy)
     if use_mlp:
         abi.mlp_set_weights(sim.ctx, mlp_w)
     stream = sim.stream
@@ -822,7 +822,9 @@ def measure_2d3v(name, device, alu, steps, warmup, e2e_steps, cold_steps, fp64_s
                    "phase_cells_per_gpu": cells,
                    "precision": "f32 f, sweeps and fluid right-hand side; f64 moment sums, fluid state, fields; "
                                 "double-float Newton fit" + ("; BF16 warm-start network" if use_mlp else ""),
-                   "splitting": "lie x,y,v; 5-shear Boris velocity map", "l2": "inputs larger than L2 (f %.1f GB)" % (
+                   "splitting": "lie x,y,v; 5-shear Boris velocity map",
+                   "spatial_sweeps": "fused x+y (pfc_advect_xy)" if fused_xy else "single-axis x then y (pfc_advect_x)",
+                   "l2": "inputs larger than L2 (f %.1f GB)" % (
                        sum(cfg.ncell * s_.vblock for s_ in cfg.species) * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof, "newton_roofline": newton,
@@ -936,6 +938,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=10, help="steps of the FP64 form timed for comparison")
     ap.add_argument("--no-mlp", action="store_true", help="cold-started fits only (no warm-start network)")
+    ap.add_argument("--single-axis", action="store_true",
+                    help="the spatial step as two single-axis sweeps (pfc_advect_x) instead of the fused x+y one")
     ap.add_argument("--train-from", default=None, choices=sorted(WORKLOADS),
                     help="workload whose fits train the warm-start network (default: the same velocity grid)")
     ap.add_argument("--harvest-steps", type=int, default=24, help="cold-started steps harvested for training")
@@ -980,7 +984,7 @@ def main():
                        harvest_steps=args.harvest_steps, train_from=args.train_from, no_mlp=args.no_mlp, dist=dist,
                        world=world, gpu_index=local,
                        transfer_from="harris_128x64_v20" if extra and not args.no_mlp else None,
-                       transfer_samples=10_000_000)
+                       transfer_samples=10_000_000, fused_xy=not args.single_axis)
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
