@@ -1,6 +1,7 @@
 // C-ABI layer of libvlasov: descriptor validation, workspace layout and the
 // entry points declared in include/vlasov.h. Every compute call only
 // enqueues kernels on the caller's stream.
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -52,6 +53,16 @@ namespace {
 
 // errors of calls without a context (per host thread)
 thread_local char g_err[512] = "";
+
+// NVTX range around a compute entry point, named after the call, so that a
+// profiler can select the kernels one call launched (ncu --nvtx
+// --nvtx-include "moment_fit_solve/"); a no-op unless a tool is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 vl_status fail(vl_ctx* ctx, vl_status st, const char* fmt, ...) {
     char* buf = ctx ? ctx->err : g_err;
@@ -286,6 +297,7 @@ vl_status vl_sync_status(vl_ctx* ctx, vl_stream_t stream) {
 const char* vl_last_error(const vl_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
 vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stream) {
+    Range nvtx_("pfc_advect_x");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     const vl_desc& d = ctx->d;
@@ -361,6 +373,7 @@ vl_status pfc_advect_x(vl_ctx* ctx, int s, int axis, double dt, vl_stream_t stre
 }
 
 vl_status pfc_advect_xy(vl_ctx* ctx, int s, double dt, void* f_out, vl_stream_t stream) {
+    Range nvtx_("pfc_advect_xy");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     const vl_desc& d = ctx->d;
@@ -436,6 +449,7 @@ vl_status pfc_advect_xy(vl_ctx* ctx, int s, double dt, void* f_out, vl_stream_t 
 }
 
 vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream_t stream) {
+    Range nvtx_("pfc_advect_v");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     const vl_desc& d = ctx->d;
@@ -457,6 +471,7 @@ vl_status pfc_advect_v(vl_ctx* ctx, int s, double dt, double* mom_out, vl_stream
 
 vl_status pfc_advect_v_static(const vl_desc* desc, int s, void* f_dev, const double* eb_dev, long long ncell,
                               double dt, double* mom_out, vl_stream_t stream) {
+    Range nvtx_("pfc_advect_v_static");
     vl_status st = validate(desc, nullptr);
     if (st != VL_OK) return st;
     const vl_desc& d = *desc;
@@ -504,6 +519,7 @@ vl_status pfc_advect_v_static(const vl_desc* desc, int s, void* f_dev, const dou
 }
 
 vl_status moments(vl_ctx* ctx, int s, double* mom_out, vl_stream_t stream) {
+    Range nvtx_("moments");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!mom_out) return fail(ctx, VL_EINVAL, "mom_out is NULL");
@@ -527,6 +543,7 @@ vl_status moment_fit_wide(vl_ctx* ctx, int s, int wide) {
 
 vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
                            vl_stream_t stream) {
+    Range nvtx_("moment_fit_solve");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
@@ -596,6 +613,7 @@ vl_status moment_fit_solve(vl_ctx* ctx, int s, const double* vmom, int use_mlp, 
 }
 
 vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, double* mom_out, vl_stream_t stream) {
+    Range nvtx_("moment_fit_exchange");
     vl_status st = check_species(ctx, s);
     if (st != VL_OK) return st;
     if (!vmom) return fail(ctx, VL_EINVAL, "vmom is NULL");
@@ -619,12 +637,14 @@ vl_status moment_fit_exchange(vl_ctx* ctx, int s, const double* vmom, double* mo
 
 vl_status moment_fit(vl_ctx* ctx, int s, const double* vmom, int use_mlp, double* theta_v, double* theta_f,
                      double* mom_out, vl_stream_t stream) {
+    Range nvtx_("moment_fit");
     vl_status st = moment_fit_solve(ctx, s, vmom, use_mlp, theta_v, theta_f, stream);
     if (st != VL_OK) return st;
     return moment_fit_exchange(ctx, s, vmom, mom_out, stream);
 }
 
 vl_status fluid_step_closure(vl_ctx* ctx, double dt, vl_stream_t stream) {
+    Range nvtx_("fluid_step_closure");
     {
         const vl_status st0 = check_ctx(ctx);
         if (st0 != VL_OK) return st0;
@@ -719,6 +739,7 @@ extern "C" {
 
 vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const double* const* mom_t1,
                      vl_stream_t stream) {
+    Range nvtx_("fluid_step");
     {
         const vl_status st0 = check_ctx(ctx);
         if (st0 != VL_OK) return st0;
@@ -733,6 +754,7 @@ vl_status fluid_step(vl_ctx* ctx, double dt, const double* const* mom_t, const d
 
 vl_status fluid_step_species(vl_ctx* ctx, int s, double dt, const double* mom_t, const double* mom_t1,
                              vl_stream_t stream) {
+    Range nvtx_("fluid_step_species");
     {
         const vl_status st0 = check_ctx(ctx);
         if (st0 != VL_OK) return st0;
@@ -742,6 +764,7 @@ vl_status fluid_step_species(vl_ctx* ctx, int s, double dt, const double* mom_t,
 }
 
 vl_status maxwell_step(vl_ctx* ctx, double h, const double* const* mom, vl_stream_t stream) {
+    Range nvtx_("maxwell_step");
     {
         const vl_status st0 = check_ctx(ctx);
         if (st0 != VL_OK) return st0;
@@ -801,6 +824,7 @@ vl_status mlp_check_err(vl_ctx* ctx, cudaStream_t cs, const char* what) {
 }  // namespace
 
 vl_status mlp_init(vl_ctx* ctx, unsigned long long seed) {
+    Range nvtx_("mlp_init");
     if (!ctx) return fail(nullptr, VL_EINVAL, "context is NULL");
     std::vector<float> w(VL_MLP_NPARAM, 0.f);
     // unit normalisation until mlp_normalize sets it from samples
@@ -863,6 +887,7 @@ vl_status mlp_harvest_count(vl_ctx* ctx, long long* n, vl_stream_t stream) {
 }
 
 vl_status mlp_normalize(vl_ctx* ctx, const float* samples_dev, long long n, vl_stream_t stream) {
+    Range nvtx_("mlp_normalize");
     if (!ctx || !samples_dev || n <= 0) return fail(ctx, VL_EINVAL, "bad samples");
     if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "call mlp_init first");
     return cuda_check(ctx, vl::launch_mlp_stats(samples_dev, n, ctx->mlp_acc, ctx->mlp_w, (cudaStream_t)stream),
@@ -871,6 +896,7 @@ vl_status mlp_normalize(vl_ctx* ctx, const float* samples_dev, long long n, vl_s
 
 vl_status mlp_train(vl_ctx* ctx, const float* samples_dev, long long n, int steps, int batch, float lr,
                     unsigned long long seed, double* loss_host, vl_stream_t stream) {
+    Range nvtx_("mlp_train");
     if (!ctx || !samples_dev || n <= 0) return fail(ctx, VL_EINVAL, "bad samples");
     if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "call mlp_init first");
     if (steps < 0 || batch < 128 || batch % 128 != 0 || batch > (1 << 24) || !(lr > 0.f))
@@ -911,6 +937,7 @@ vl_status mlp_train(vl_ctx* ctx, const float* samples_dev, long long n, int step
 }
 
 vl_status mlp_forward(vl_ctx* ctx, const float* x_dev, long long n, float* y_dev, vl_stream_t stream) {
+    Range nvtx_("mlp_forward");
     if (!ctx || n < 0 || (n > 0 && (!x_dev || !y_dev))) return fail(ctx, VL_EINVAL, "bad arguments");
     if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "no MLP weights on this context");
     vl::MlpInferArgs m = {};
@@ -928,6 +955,7 @@ vl_status mlp_forward(vl_ctx* ctx, const float* x_dev, long long n, float* y_dev
 
 vl_status mlp_grad(vl_ctx* ctx, const float* samples_dev, long long n, float* grad_dev, double* loss_host,
                    vl_stream_t stream) {
+    Range nvtx_("mlp_grad");
     if (!ctx || !samples_dev || n <= 0 || !grad_dev) return fail(ctx, VL_EINVAL, "bad arguments");
     if (!ctx->mlp_ready) return fail(ctx, VL_EINVAL, "no MLP weights on this context");
     cudaStream_t cs = (cudaStream_t)stream;
