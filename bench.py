@@ -351,7 +351,7 @@ def cpu_baseline(name, steps=1, sample=(32, 16)):
     el = time.perf_counter() - t0
     cells = cfg.phase_cells() * steps
     nv = cfg.species[0].nv[0]
-    return {"value": cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": cells / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample_ms_per_step": 1e3 * el / steps,
             "sample": "%d oracle step(s) of the %s sheet on a %dx%d x %d^3 subdomain (2 species, %d cells, "
                       "same dx, dv, dt as the workload), FP64, one host core, %.1f s" % (
                           steps, cfg.kind, cfg.nx, cfg.ny, nv, cfg.phase_cells(), el)}
@@ -533,13 +533,15 @@ def run_reference(args, rank):
             st.step(cfg.dt)
         el = time.perf_counter() - t0
         cb = {"value": cfg.phase_cells() * args.steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample_ms_per_step": 1e3 * el / args.steps,
               "sample": "the whole workload, %d oracle steps, FP64, one host core, %.2f s" % (args.steps, el)}
     else:
         cb = cpu_baseline(args.workload, steps=args.steps, sample=(16, 8))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "ms_per_step": None,
+            # a step of the whole workload only where the oracle ran the whole workload
+            "ms_per_step": cb["sample_ms_per_step"] if args.workload == LANDAU else None,
             "config": {"workload": args.workload + (" (the whole workload)" if args.workload == LANDAU
                                                     else " (oracle sample: 16x8 spatial subdomain)")},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
