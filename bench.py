@@ -137,12 +137,16 @@ class ClockSampler:
 # of the Gram matrix beyond the moments) when the Jacobian is formed.
 METHOD_OPS_MOMENT = 10
 METHOD_OPS_GRAM = 25
-# What the double-float kernel issues on the FP32 pipe for the same work:
-# two double-float products for the recurrence, three compensated
-# accumulations and the index step (46), plus the FP32 sums of degree <= 4
-# when the Jacobian is formed in the same pass (7), counted operation by
-# operation.
-ISSUED_OPS_MOMENT_DF = 46
+# What the double-float kernels issue on the FP32 (FMA) pipe for the same
+# work, counted operation by operation: two double-float products for the
+# recurrence, three compensated accumulations and the index step -- 37 in
+# the edge-start pass of the common kernel, whose accumulations order their
+# operands on the ALU pipe (7 more operations there) and add by Fast2Sum,
+# 46 in the centre-out pass of the wide kernel (TwoSum) -- plus the FP32
+# sums of degree <= 4 when the Jacobian is formed in the same pass (7).
+ISSUED_OPS_MOMENT_EDGE = 37
+ISSUED_ALU_OPS_MOMENT_EDGE = 7
+ISSUED_OPS_MOMENT_CENTRE = 46
 ISSUED_OPS_GRAM_DF = 7
 # What the FP64 kernel issues on the FP64 pipe: the two products of the
 # recurrence and three accumulations (5), plus two accumulations with the
@@ -153,13 +157,13 @@ ISSUED_OPS_GRAM_64 = 2
 # not) and velocity grid, from ncu captures of the current kernels on the
 # 256 x 128 Harris sheet (dram__bytes_read.sum + dram__bytes_write.sum over
 # 32768 cells; scaled by the cell count, as the traffic is per cell): the
-# double-float kernel warm-started, 39.58 MB (targets, coefficients, status,
+# double-float kernel warm-started, 39.90 MB (targets, coefficients, status,
 # predictions and its local memory), the FP64 kernel cold-started, 8.20 MB
 # (its coefficient writes stay in L2 during the launch). A grid not captured
 # gives None.
 # timed runs of the end-to-end leg (the fastest is reported, all are listed)
 E2E_REPS = 8
-NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.257856e6 / 32768, (True, 16): 8.204032e6 / 32768}
+NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.895808e6 / 32768, (True, 16): 8.204032e6 / 32768}
 # Bytes a fit launch must move per cell: the 20 raw moments (read), the fluid
 # state (10 doubles read and written), both Maxwellians' 16 coefficients
 # (written), the status pair and, warm-started, the network's 20 predictions.
@@ -201,7 +205,10 @@ def newton_roofline(cfg, stats, fit_ms, launches, alu, fp64=False):
         evals = {"moments": em, "gram": eg}
     else:
         em, eg = stats[4] + stats[6], stats[5] + stats[7]
-        issued = (ISSUED_OPS_MOMENT_DF * em + ISSUED_OPS_GRAM_DF * eg) * n3
+        # the wide kernel takes whole species: its share of the fits
+        w = min(1.0, stats[9] / max(1, 2 * cfg.ncell * launches))
+        issued = ((ISSUED_OPS_MOMENT_EDGE * (1 - w) + ISSUED_OPS_MOMENT_CENTRE * w) * em + ISSUED_OPS_GRAM_DF * eg) * n3
+        issued_alu = ISSUED_ALU_OPS_MOMENT_EDGE * (1 - w) * em * n3
         peak = alu["fp32_tops"]
         kernel, pipe = "fit_solve (newton_kernel, double-float on the FP32 pipe)", "FP32"
         evals = {"moments": stats[4], "gram": stats[5], "slow": stats[6], "precise_steps": stats[7],
@@ -219,6 +226,7 @@ def newton_roofline(cfg, stats, fit_ms, launches, alu, fp64=False):
            "evaluations": evals}
     if not fp64:
         out["method_vs_fp64_peak"] = achieved / alu["fp64_tops"]
+        out["issued_alu_ops_per_launch"] = issued_alu / max(1, launches)
     return out
 
 
