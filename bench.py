@@ -139,18 +139,19 @@ METHOD_OPS_MOMENT = 10
 METHOD_OPS_GRAM = 25
 # What the double-float kernels issue on the FP32 (FMA) pipe for the same
 # work, counted operation by operation: two double-float products for the
-# recurrence, three compensated accumulations and the index step -- 31 in
+# recurrence, three compensated accumulations and the index step -- 30 in
 # the edge-start pass of the common kernel, whose accumulations order their
-# operands on the ALU pipe (7 more operations there) and add by Fast2Sum
-# and whose products skip the renormalisation (the ratio's always, the
-# value's without the Jacobian: 3 operations each; counted here as in the
-# moment-only pass), 43 in the centre-out pass of the wide kernel (TwoSum,
-# the ratio unnormalised) -- plus the FP32 sums of degree <= 4 and the
-# value's renormalisation when the Jacobian is formed in the same pass (10).
-ISSUED_OPS_MOMENT_EDGE = 31
+# operands on the ALU pipe (7 more operations there), add by Fast2Sum and
+# take their weighted terms as chained products, and whose products skip
+# the renormalisation (the ratio's always, the value's without the
+# Jacobian; counted here as in the moment-only pass), 43 in the centre-out
+# pass of the wide kernel (TwoSum, the ratio unnormalised) -- plus the FP32
+# sums of degree <= 4 and the value's renormalisation when the Jacobian is
+# formed in the same pass (9).
+ISSUED_OPS_MOMENT_EDGE = 30
 ISSUED_ALU_OPS_MOMENT_EDGE = 7
 ISSUED_OPS_MOMENT_CENTRE = 43
-ISSUED_OPS_GRAM_DF = 10
+ISSUED_OPS_GRAM_DF = 9
 # What the FP64 kernel issues on the FP64 pipe: the two products of the
 # recurrence and three accumulations (5), plus two accumulations with the
 # Gram sums (2).
@@ -160,13 +161,13 @@ ISSUED_OPS_GRAM_64 = 2
 # not) and velocity grid, from ncu captures of the current kernels on the
 # 256 x 128 Harris sheet (dram__bytes_read.sum + dram__bytes_write.sum over
 # 32768 cells; scaled by the cell count, as the traffic is per cell): the
-# double-float kernel warm-started, 39.94 MB (targets, coefficients, status,
+# double-float kernel warm-started, 36.66 MB (targets, coefficients, status,
 # predictions and its local memory), the FP64 kernel cold-started, 8.20 MB
 # (its coefficient writes stay in L2 during the launch). A grid not captured
 # gives None.
 # timed runs of the end-to-end leg (the fastest is reported, all are listed)
 E2E_REPS = 8
-NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 39.942912e6 / 32768, (True, 16): 8.204032e6 / 32768}
+NEWTON_DRAM_BYTES_PER_CELL = {(False, 16): 36.659200e6 / 32768, (True, 16): 8.204032e6 / 32768}
 # Bytes a fit launch must move per cell: the 20 raw moments (read), the fluid
 # state (10 doubles read and written), both Maxwellians' 16 coefficients
 # (written), the status pair and, warm-started, the network's 20 predictions.
